@@ -1,0 +1,87 @@
+/*
+ * kerr_oracle.h -- plain, slow FP64 CPU oracle for backward ray tracing and
+ * radiative transfer in Kerr spacetime (Pu, Yun, Younsi & Yoon 2016, "Odyssey").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may include, link or
+ * call this code: only the test suite, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no source, header, table or helper with
+ * the CUDA library; the two sides meet only through the scene numbers a caller
+ * passes to each.
+ *
+ * Units: G = c = M = 1 (Section 2).  The traced photon has E = 1.
+ */
+#ifndef KERR_ORACLE_H
+#define KERR_ORACLE_H
+
+#include <stdint.h>
+
+#define ORC_MAX_FREQ 8
+
+/* ray status after tracing */
+#define ORC_RUNNING 0
+#define ORC_ESCAPED 1
+#define ORC_CAPTURED 2
+#define ORC_DISK_HIT 3
+#define ORC_MAXSTEPS 4
+#define ORC_NUMERR 5
+
+/* emission models */
+#define ORC_EMIT_NONE 0      /* grid projection / shadow: geodesics only        */
+#define ORC_EMIT_THIN_DISK 1 /* opaque Keplerian equatorial disk, I = g^4 r^-q  */
+#define ORC_EMIT_TORUS 2     /* analytic thermal torus, RT Eqs. 30-31           */
+#define ORC_EMIT_CONST 3     /* test medium: dtau/ds = kappa, dI/ds = eps e^-tau */
+
+/* sign conventions for the traced photon (see the direction reading in the design notes) */
+#define ORC_CONV_PHYSICAL 0 /* real outgoing photon, traced back in affine time */
+#define ORC_CONV_LITERAL 1  /* future-directed inward photon, Eqs. 24-26 as printed */
+
+typedef struct {
+    double a, r_obs, theta_obs, phi_obs;
+    double alpha_min, alpha_max, beta_min, beta_max;
+    int32_t n_alpha, n_beta;
+    int32_t emitter;
+    int32_t n_freq;
+    double freqs[ORC_MAX_FREQ];
+    double r_in, r_out, q_emis;        /* thin disk; r_in <= 0 means r_ISCO(a) */
+    double ne_index, theta_width;      /* torus: n_e = r^-ne_index exp(-cos^2/(2 w^2)) */
+    double T0, T_index;                /* torus: T_e = T0 r^-T_index */
+    double C_norm;                     /* torus emissivity normalisation;
+                                          const medium: kappa = C_norm, eps = T0 */
+    double rtol, h0, hmax_frac, horizon_factor;
+    int32_t max_steps;
+    int32_t convention;
+} orc_scene;
+
+typedef struct {
+    int32_t status, n_acc, n_rej, n_cross;
+    double r_cross, phi_cross;         /* first equatorial crossing (NaN if none) */
+    double r_hit, phi_hit, g, intensity; /* thin-disk hit (NaN / 0 otherwise)      */
+    double H_end, Q_drift;             /* relative null violation, relative Q drift */
+    double s_end;                      /* affine length traced                     */
+    double L, Q0;                      /* constants of motion of the ray (E = 1)   */
+    double y_end[6];                   /* r, theta, phi, t, p_r, p_theta at the end */
+    double I_nu[ORC_MAX_FREQ];         /* observed I_nu = nu^3 * invariant I      */
+    double tau_nu[ORC_MAX_FREQ];
+} orc_result;
+
+double orc_horizon(double a);
+double orc_isco(double a);
+void orc_ck_tableau(double c[6], double a[36], double b5[6], double b4[6]);
+void orc_pixel_center(const orc_scene *sc, int32_t i, int32_t j, double *alpha, double *beta);
+void orc_observer_point(const orc_scene *sc, double alpha, double beta, double xyz[3]);
+void orc_init_ray(const orc_scene *sc, double alpha, double beta, double y0[6], double *L,
+                  double *Q, double vin[3]);
+void orc_geodesic_rhs(double a, double L, const double y[6], double f[6]);
+double orc_disk_redshift(double a, double r, double L);
+double orc_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
+                      double r_outer);
+int orc_trace_ray(const orc_scene *sc, double alpha, double beta, orc_result *out);
+int orc_trace_path(const orc_scene *sc, double alpha, double beta, int32_t max_pts,
+                   double *s_pts, double *y_pts, int32_t *n_pts, orc_result *out);
+int orc_render(const orc_scene *sc, const int64_t *pixels, int64_t n, orc_result *out,
+               int32_t n_threads);
+int orc_trace_list(const orc_scene *proto, const double *rays, int64_t n, orc_result *out,
+                   int32_t n_threads);
+int orc_max_threads(void);
+
+#endif

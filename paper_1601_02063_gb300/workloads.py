@@ -1,0 +1,105 @@
+"""Seeded synthetic workloads shared by the CUDA path and the oracle.
+
+This module holds only scene parameters and seeded random draws: none of the
+method's arithmetic.  Quantities that the method derives (r_ISCO for a disk with
+``r_in = 0``, the torus emissivity normalisation when ``C_norm`` is None) are left
+for each side to compute with its own code.
+
+The scenes follow the workloads of Pu et al. 2016: thin Keplerian disk around a Kerr
+hole seen from r = 1000 M (Sections 4.1-4.3, Table 1's grid-projection workload),
+analytic thermal flow for the radiative transfer of Section 2.3, a many-scene
+parameter sweep, and a 4096^2 near-edge-on case.  All randomness draws from numpy's
+PCG64 with an explicit seed.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 20160109
+
+_DEFAULTS = dict(
+    a=0.9, r_obs=1000.0, theta_obs=math.radians(60.0), phi_obs=0.0,
+    alpha_min=-15.0, alpha_max=15.0, beta_min=-15.0, beta_max=15.0,
+    n_alpha=64, n_beta=64, emitter="thin_disk", freqs=[],
+    r_in=0.0, r_out=20.0, q_emis=3.0,
+    ne_index=1.5, theta_width=0.3, T0=10.0, T_index=0.84, C_norm=None, nu_norm=1.0,
+    rtol=1e-8, h0=1.0, hmax_frac=0.1, horizon_factor=1.01, max_steps=100000,
+    convention="physical", precision="fp64",
+    # reduced-precision controls (ignored by the FP64 path)
+    rtol_fp32=1e-6, r_switch=0.0,
+)
+
+
+def scene(**kw) -> dict:
+    """A scene dict with the defaults above overridden by ``kw``."""
+    unknown = set(kw) - set(_DEFAULTS)
+    if unknown:
+        raise KeyError(f"unknown scene keys: {sorted(unknown)}")
+    d = dict(_DEFAULTS)
+    d.update(kw)
+    d["freqs"] = list(d["freqs"])
+    return d
+
+
+def thin_disk_64() -> dict:
+    """Kerr a=0.9, r_obs=1000, i=60 deg, 64x64 over [-15,15]^2, thin Keplerian disk from
+    r_ISCO to 20 M with emissivity r^-3, Cash-Karp rtol 1e-8."""
+    return scene()
+
+
+def torus_512(precision: str = "fp64") -> dict:
+    """a=0.94, i=30 deg, r_obs=1000, 512x512 over [-20,20]^2; analytic Keplerian torus
+    n_e = r^-1.5 exp(-cos^2 / (2 0.3^2)), T_e = 10 r^-0.84, thermal emission with Kirchhoff
+    absorption at nu in {0.5, 1, 2}; stop at 1.01 r_+ or on escape."""
+    return scene(a=0.94, theta_obs=math.radians(30.0), alpha_min=-20.0, alpha_max=20.0,
+                 beta_min=-20.0, beta_max=20.0, n_alpha=512, n_beta=512, emitter="torus",
+                 freqs=[0.5, 1.0, 2.0], precision=precision)
+
+
+def torus_hard_4096(precision: str = "mixed") -> dict:
+    """a=0.998, i=85 deg, 4096x4096 over [-20,20]^2, torus as above at 8 log-spaced
+    frequencies in [0.25, 4]."""
+    freqs = [float(v) for v in np.geomspace(0.25, 4.0, 8)]
+    return scene(a=0.998, theta_obs=math.radians(85.0), alpha_min=-20.0, alpha_max=20.0,
+                 beta_min=-20.0, beta_max=20.0, n_alpha=4096, n_beta=4096, emitter="torus",
+                 freqs=freqs, precision=precision)
+
+
+def sweep_64(seed: int = SEED, precision: str = "mixed") -> list[dict]:
+    """64 thin-disk scenes: resolution from {128,256,512,1024}^2, a ~ U[0, 0.998],
+    i ~ U[5, 85] deg, disk and window as in the 64x64 thin-disk scene."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    res = rng.choice([128, 256, 512, 1024], size=64)
+    spins = rng.uniform(0.0, 0.998, size=64)
+    incl = rng.uniform(5.0, 85.0, size=64)
+    return [scene(a=float(a), theta_obs=math.radians(float(i)), n_alpha=int(n), n_beta=int(n),
+                  precision=precision)
+            for n, a, i in zip(res, spins, incl)]
+
+
+def training_rays(n: int, seed: int = SEED + 1) -> np.ndarray:
+    """n rays (alpha, beta, a, cos i): alpha, beta ~ U[-20, 20], a ~ U[0, 0.998],
+    i ~ U[1, 89] deg.  Returns float64 [n, 4]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((n, 4), dtype=np.float64)
+    out[:, 0] = rng.uniform(-20.0, 20.0, n)
+    out[:, 1] = rng.uniform(-20.0, 20.0, n)
+    out[:, 2] = rng.uniform(0.0, 0.998, n)
+    out[:, 3] = np.cos(np.radians(rng.uniform(1.0, 89.0, n)))
+    return out
+
+
+def surrogate_scene_2048() -> dict:
+    """Inference image for the learned transfer function: 2048^2 thin disk, a=0.7,
+    i=45 deg, window [-20,20]^2."""
+    return scene(a=0.7, theta_obs=math.radians(45.0), alpha_min=-20.0, alpha_max=20.0,
+                 beta_min=-20.0, beta_max=20.0, n_alpha=2048, n_beta=2048, precision="mixed")
+
+
+def sample_pixels(n_pix: int, k: int, seed: int = SEED + 2) -> np.ndarray:
+    """k distinct flat pixel indices out of n_pix, sorted."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = min(k, n_pix)
+    return np.sort(rng.choice(n_pix, size=k, replace=False)).astype(np.int64)
