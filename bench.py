@@ -1,0 +1,339 @@
+"""Benchmark: backward ray tracing + radiative transfer of one 512x512 image per step.
+
+Workload: Kerr a = 0.94, r_obs = 1000 M, inclination 30 deg, 512 x 512 pixels over
+[-20, 20]^2 M, analytic thermal torus at nu = 0.5, 1, 2 (the GRRT workload).  One step
+renders the whole image through the C ABI (initial conditions, Cash-Karp integration,
+termination, redshift and transfer).  Metric: ns per photon per Runge-Kutta step
+(= kernel time / attempted steps summed over all rays), plus images/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun (N > 1) each rank renders its own image (independent problems, no
+collective); value aggregates all ranks' steps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ns per photon per RK step; images/s at <=1e-3 rel image error vs plain FP64 path"
+UNIT = "ns/photon/step"
+WORKLOAD = "torus512"
+
+
+# Algorithmic flops per attempted Runge-Kutta step, counted from the formulas of the
+# method (add, sub, mul, div, sqrt, each transcendental = 1 flop; a fused multiply-add is
+# counted as its two operations).  Derivation in the design doc (per-unit work).
+FLOPS_GEODESIC_STEP = 895.0       # 6 right-hand sides x 90 + stage sums 210 + solution
+                                  # and error 114 + error norm and step control 31
+FLOPS_TORUS_STAGE_BASE = 57.0     # flow, redshift, n_e, T_e per stage
+FLOPS_TORUS_STAGE_PER_NU = 19.0   # per frequency per stage
+FLOPS_RT_SUMS_PER_NU = 54.0       # stage and solution sums of tau, I per frequency
+
+
+def flops_per_step(scene: dict) -> float:
+    f = FLOPS_GEODESIC_STEP
+    if scene["emitter"] == "torus":
+        nf = len(scene["freqs"])
+        f += 6 * (FLOPS_TORUS_STAGE_BASE + FLOPS_TORUS_STAGE_PER_NU * nf) + FLOPS_RT_SUMS_PER_NU * nf
+    return f
+
+
+def read_traffic(workload, precision):
+    """DRAM bytes per launch of the tracer from the committed ncu summary (None if the
+    kernel has no capture for this workload)."""
+    path = os.path.join(ROOT, "profiles", "trace_traffic.txt")
+    if workload is None or not os.path.exists(path):
+        return None
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and not ln.startswith("#") and parts[0] == workload \
+                and parts[1] == precision:
+            return int(parts[2])
+    return None
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bench_scene(precision: str, size: int = 512) -> dict:
+    from paper_1601_02063_gb300 import workloads as W
+    sc = W.torus_512(precision=precision)
+    sc.update(n_alpha=size, n_beta=size)
+    return sc
+
+
+def cpu_oracle_sample(scene: dict, target_s: float = 12.0):
+    """Time the FP64 oracle on a bounded, stratified pixel sample of the workload (every
+    stride-th pixel of every stride-th row), sized to take about target_s seconds."""
+    import numpy as np
+    import oracle
+    from paper_1601_02063_gb300 import workloads as W
+
+    oracle.build()
+    threads = oracle.default_threads()
+    n = scene["n_alpha"] * scene["n_beta"]
+    probe = W.sample_pixels(n, 256, seed=W.SEED + 7)
+    sc = dict(scene, precision="fp64")
+    t0 = time.perf_counter()
+    res = oracle.render(sc, pixels=probe, threads=threads)
+    dt = time.perf_counter() - t0
+    per_ray = dt / len(probe)
+    k = int(max(256, min(n, target_s / max(per_ray, 1e-9))))
+    stride = max(1, int(math.sqrt(n / k)))
+    jj, ii = np.meshgrid(np.arange(0, scene["n_beta"], stride),
+                         np.arange(0, scene["n_alpha"], stride), indexing="ij")
+    pix = (jj * scene["n_alpha"] + ii).ravel().astype(np.int64)
+    t0 = time.perf_counter()
+    res = oracle.render(sc, pixels=pix, threads=threads)
+    dt = time.perf_counter() - t0
+    steps = int(res["n_acc"].sum() + res["n_rej"].sum())
+    return {"value": dt * 1e9 / steps, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(pix)} pixels (every {stride}th pixel of every {stride}th row of "
+                      f"the {scene['n_alpha']}x{scene['n_beta']} image), {steps} RK steps, "
+                      f"{dt:.2f} s wall",
+            "seconds": dt, "steps": steps, "rays": len(pix)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    scene = bench_scene("fp64", args.size)
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_oracle_sample(scene, target_s=2.0)
+    vals, secs = [], []
+    info = None
+    for _ in range(args.steps):
+        info = cpu_oracle_sample(scene, target_s=8.0)
+        vals.append(info["value"])
+        secs.append(info["seconds"])
+    value = sum(v * s for v, s in zip(vals, secs)) / sum(secs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": "512x512", "a": 0.94, "inclination_deg": 30,
+                   "n_freq": 3, "sample": info["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"],
+                         "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1601_02063_gb300 import binding as B
+    from paper_1601_02063_gb300 import build as cuda_build
+
+    cuda_build.build()
+    scene = bench_scene(args.precision, args.size)
+    tr = B.Tracer(local)
+    n = B.n_rays(scene)
+    rec, img = tr.alloc(n, B.n_image(scene))
+    stream = torch.cuda.current_stream(local)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        tr.render(scene, out=(rec, img))
+    barrier()
+    tr.stats(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    barrier()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed iterations (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr.render(scene, out=(rec, img), stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    clk = clocks.stop()
+    st = tr.stats(reset=True)
+    total_ms = sum(times)
+    steps_local = st["steps_accepted"] + st["steps_rejected"]
+    t = torch.tensor([total_ms, float(steps_local), float(st["rays"])], dtype=torch.float64,
+                     device=f"cuda:{local}")
+    if world > 1:
+        import torch.distributed as dist
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:3], op=dist.ReduceOp.SUM)
+        t[0] = tmax[0]
+    total_ms, steps_all, rays_all = float(t[0]), float(t[1]), float(t[2])
+    value = total_ms * 1e6 / steps_all
+    ms_per_step = total_ms / args.steps
+
+    # roofline of the tracing kernel (the only kernel of the step)
+    peak = B.odx_fma_peak(tr.ctx, "fp64" if args.precision == "fp64" else "mixed")
+    flops = flops_per_step(scene) * steps_local
+    achieved = flops / (sum(times) * 1e-3)
+    traffic = read_traffic(WORKLOAD if args.size == 512 else None, args.precision)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    rec_h = torch.empty(n * B.RECORD_BYTES // 8, dtype=torch.float64).pin_memory().numpy()
+    img_h = torch.empty(B.n_image(scene), dtype=torch.float64).pin_memory().numpy()
+    rec_h = rec_h.view(np.uint8).view(B.RECORD_DTYPE)
+    B.odx_render_host(tr.ctx, [scene], rec_h, img_h)
+    tr.stats(reset=True)
+    e2e_s = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.odx_render_host(tr.ctx, [scene], rec_h, img_h)
+        e2e_s.append(time.perf_counter() - t0)
+    st2 = tr.stats(reset=True)
+    e2e_steps = (st2["steps_accepted"] + st2["steps_rejected"]) / len(e2e_s)
+    e2e_value = statistics.mean(e2e_s) * 1e9 / e2e_steps
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = cpu_oracle_sample(scene) if world == 1 and not args.skip_cpu else None
+    if cpu:
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.size == 512 else f"torus{args.size}",
+                   "image": f"{args.size}x{args.size}", "a": 0.94, "inclination_deg": 30,
+                   "r_obs": 1000, "window": "[-20,20]^2", "emitter": "torus", "n_freq": 3,
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MB)",
+                   "launch": B.odx_get_launch(tr.ctx)},
+        "images_per_s": 1e3 / ms_per_step * world,
+        "steps_per_photon": steps_all / rays_all,
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "measured FMA-chain microbenchmark, same run",
+                     "pipe": "fp64" if args.precision == "fp64" else "fp32"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 304,
+                "d2h_bytes_per_step": n * B.RECORD_BYTES + 8 * B.n_image(scene)},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "paper_context": {"value": 16.31, "unit": "ns per RK step (runtime / total steps)",
+                          "hardware": "GeForce GTX 780 Ti, FP64, 1024^2 grid projection"},
+    }
+    print(json.dumps(line), flush=True)
+    tr.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--size", type=int, default=512,
+                    help="image side (the workload is 512; smaller sizes are for profiling)")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

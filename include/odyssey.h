@@ -1,0 +1,217 @@
+/*
+ * odyssey.h -- C ABI of the GB300 (sm_103a) library for backward ray tracing and
+ * general-relativistic radiative transfer in Kerr spacetime, after Pu, Yun, Younsi &
+ * Yoon 2016 ("Odyssey: a public GPU-based code for GRRT in Kerr spacetime").
+ *
+ * Units: G = c = M = 1 (Section 2).  Every traced photon has E = 1.
+ *
+ * Conventions shared by all calls
+ *   - Pointers named *_dev are device pointers on the context's device; *_host are host
+ *     pointers.  All output buffers are owned by the caller; the library owns only its
+ *     context scratch (ray queue counters, statistics, scene table, error flag).
+ *   - Calls that take a `stream` (a cudaStream_t, NULL = legacy default stream) are
+ *     asynchronous on that stream; the caller must not reuse outputs before the stream
+ *     reaches them.  Calls on one context must not overlap on different streams: the
+ *     context's scratch is shared.
+ *   - Every call returns an odx status code (0 = ODX_OK).  Invalid arguments are rejected
+ *     before any launch with ODX_ERR_INVALID_ARG and leave outputs untouched; CUDA
+ *     failures return ODX_ERR_CUDA.  odx_last_error() gives the message of the last failure
+ *     on a context.  No C++ exception crosses this interface.
+ *   - Per-ray outcomes are statuses in the ray record, not errors.
+ */
+#ifndef ODYSSEY_H
+#define ODYSSEY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ODX_MAX_FREQ 8
+
+/* return codes */
+#define ODX_OK 0
+#define ODX_ERR_INVALID_ARG 1
+#define ODX_ERR_CUDA 2
+#define ODX_ERR_TIMEOUT 3
+#define ODX_ERR_DEVICE_FLAG 4 /* a kernel raised its device error flag (see odx_stats) */
+#define ODX_ERR_NO_DEVICE 5
+#define ODX_ERR_UNSUPPORTED 6
+
+/* ray status written to odx_ray_record.status */
+#define ODX_RUNNING 0
+#define ODX_ESCAPED 1  /* moving outward beyond its starting radius              */
+#define ODX_CAPTURED 2 /* r < horizon_factor * r_+                               */
+#define ODX_DISK_HIT 3 /* crossed the equator with r_in <= r <= r_out (thin disk) */
+#define ODX_MAXSTEPS 4 /* max_steps Runge-Kutta attempts without terminating     */
+#define ODX_NUMERR 5   /* step size underflow (|h| < 1e-12) or non-finite state  */
+
+/* emission models */
+#define ODX_EMIT_NONE 0      /* geodesics only: grid projection, shadows (Sections 4.1-4.2) */
+#define ODX_EMIT_THIN_DISK 1 /* opaque Keplerian equatorial disk, I = g^4 r^-q (Section 4.3) */
+#define ODX_EMIT_TORUS 2     /* analytic thermal flow, radiative transfer Eqs. 30-31         */
+
+/* arithmetic of the integrator */
+#define ODX_FP64 0  /* every stage in FP64                                             */
+#define ODX_MIXED 1 /* FP32 stages in bulk, FP64 within r_switch, compensated sums     */
+
+/* direction reading of the traced photon */
+#define ODX_CONV_PHYSICAL 0 /* the real outgoing photon traced back in affine time (default) */
+#define ODX_CONV_LITERAL 1  /* Eqs. 24-26 taken as the velocity of the traced photon        */
+
+/*
+ * One image (Sections 2.2, 3 and 4).  Pixel (i, j), i along alpha, j along beta, sits at
+ * alpha_i = alpha_min + (i + 1/2)(alpha_max - alpha_min)/n_alpha (same for beta); flat
+ * pixel index p = j * n_alpha + i.  The observer is at (r_obs, theta_obs, phi_obs)
+ * (Eqs. 18-19); the ray through a pixel leaves the image plane perpendicular to it.
+ */
+typedef struct odx_scene {
+    double a;                       /* spin, |a| < 1                                    */
+    double r_obs, theta_obs, phi_obs; /* observer distance (> 10 r_+), inclination in
+                                       [0, pi], azimuth (radians)                      */
+    double alpha_min, alpha_max, beta_min, beta_max; /* image window (M), min < max       */
+    int32_t n_alpha, n_beta;        /* resolution, >= 1 each                             */
+    int32_t emitter;                /* ODX_EMIT_*                                        */
+    int32_t n_freq;                 /* torus: 1..ODX_MAX_FREQ observed frequencies      */
+    double freqs[ODX_MAX_FREQ];     /* observed frequencies nu_obs (dimensionless)      */
+    double r_in, r_out, q_emis;     /* thin disk edges (r_in <= 0: r_ISCO(a)), index q   */
+    double ne_index, theta_width;   /* torus n_e = r^-ne_index exp(-cos^2 / (2 w^2))    */
+    double T0, T_index;             /* torus T_e = T0 r^-T_index                         */
+    double C_norm;                  /* torus emissivity normalisation (odx_torus_norm)  */
+    double rtol;                    /* Cash-Karp relative tolerance (FP64 stages)       */
+    double h0;                      /* first step in affine parameter                  */
+    double hmax_frac;               /* |h| <= hmax_frac * r                             */
+    double horizon_factor;          /* stop when r < horizon_factor * r_+ (> 1)         */
+    int32_t max_steps;              /* cap on Runge-Kutta attempts per ray (>= 1)       */
+    int32_t convention;             /* ODX_CONV_*                                        */
+    int32_t precision;              /* ODX_FP64 or ODX_MIXED                             */
+    int32_t reserved;               /* must be 0                                         */
+    double rtol_fp32;               /* ODX_MIXED: relative tolerance of the FP32 stages  */
+    double r_switch;                /* ODX_MIXED: FP64 stages where r < r_switch         */
+} odx_scene;
+
+/*
+ * Per-ray result, 80 bytes, written once per ray with 16-byte vector stores
+ * (the record array must be 16-byte aligned).
+ *   r_cross, phi_cross: first equatorial crossing (NaN if none), Section 4.1.
+ *   r_hit, phi_hit, g, intensity: thin-disk hit, g from Eq. 2 and I = g^4 r^-q (Section 4.3);
+ *     NaN / 0 if the ray did not hit the disk.
+ *   H_end: relative violation of the null condition at the end,
+ *     (2 Sigma H) / (sum of the magnitudes of its terms);
+ *   Q_drift: (Q_end - Q_0) / max(|Q_0|, 1), Carter constant Eq. 13.
+ *   n_acc, n_rej: accepted and rejected Runge-Kutta steps (n_acc + n_rej = attempts).
+ */
+typedef struct odx_ray_record {
+    int32_t status, n_acc, n_rej, n_cross;
+    double r_cross, phi_cross;
+    double r_hit, phi_hit, g, intensity;
+    double H_end, Q_drift;
+} odx_ray_record;
+
+/* Launch shape of the persistent tracing kernels. */
+typedef struct odx_launch {
+    int32_t block;         /* threads per block, multiple of 32, 32..1024          */
+    int32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (>= 1)  */
+    int32_t chunk;         /* rays a warp takes from the global queue at a time    */
+    int32_t persistent;    /* 1: persistent warps refilling lanes from the queue;
+                              0: one ray per thread, no queue                       */
+} odx_launch;
+
+/* Counters accumulated on the device by every tracing launch since the last reset. */
+typedef struct odx_stats {
+    int64_t rays;           /* rays finished                                        */
+    int64_t steps_accepted; /* accepted Runge-Kutta steps                           */
+    int64_t steps_rejected; /* rejected Runge-Kutta steps                           */
+    int64_t steps_fp64;     /* attempts taken with FP64 stages (ODX_MIXED)           */
+    int64_t lane_slots;     /* warp iterations x 32                                  */
+    int64_t lane_active;    /* lanes holding a live ray summed over warp iterations */
+    int32_t error_flag;     /* nonzero: a kernel met an invalid internal state     */
+    int32_t reserved;
+} odx_stats;
+
+typedef struct odx_ctx odx_ctx;
+
+/* Library version string. */
+const char *odx_version(void);
+
+/* Human-readable text of a return code. */
+const char *odx_error_string(int32_t code);
+
+/* Message of the last failure on ctx (empty string if none); valid until the next call. */
+const char *odx_last_error(const odx_ctx *ctx);
+
+/* Create a context on CUDA device `device` (ordinal) and allocate its scratch.
+ * Returns ODX_ERR_NO_DEVICE if the device does not exist or is not sm_103. */
+int32_t odx_create(odx_ctx **out, int32_t device);
+
+/* Release the context and its scratch; NULL is accepted. */
+int32_t odx_destroy(odx_ctx *ctx);
+
+/* Set / read the launch shape (validated: see odx_launch). */
+int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *launch);
+int32_t odx_get_launch(const odx_ctx *ctx, odx_launch *launch);
+
+/*
+ * Render n_scenes images in ONE persistent launch (Section 3: one ray per pixel; the rays of
+ * all scenes share one queue).  Per ray: initial state from the image plane (Section 2.2,
+ * Eqs. 18-26, 7, 8, 4, 5, 13), adaptive Cash-Karp integration of the geodesic equations
+ * (Section 2.1, Eqs. 4, 5, 9, 12, 14, 15), termination and disk crossing, redshift (Eq. 2)
+ * and radiative transfer (Section 2.3, Eqs. 30-31).
+ *   scenes_host:  n_scenes >= 1 scene descriptions (host memory, copied during the call).
+ *                 All scenes of one call must share emitter, precision and, for the torus,
+ *                 n_freq.
+ *   records_dev:  sum_k n_alpha_k n_beta_k records, scene k's pixels after scene k-1's.
+ *   image_dev:    sum_k nf_k n_alpha_k n_beta_k doubles (nf = n_freq for the torus, else 1),
+ *                 scene by scene, each [nf][n_beta][n_alpha]: I_nu,obs = nu^3 * invariant I
+ *                 for the torus, g^4 r^-q for the thin disk, 0 without emitter.  May be NULL.
+ */
+int32_t odx_render(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
+                   odx_ray_record *records_dev, double *image_dev, void *stream);
+
+/*
+ * Trace an explicit ray list (training data for the learned transfer function, fallback
+ * pixels).  rays_dev[n][4] = (alpha, beta, a, cos i) in device memory; every other scene
+ * parameter from proto_host (its window and resolution are ignored).  records_dev[n];
+ * image_dev [nf][n] or NULL.  n == 0 is a no-op.
+ */
+int32_t odx_trace_rays(odx_ctx *ctx, const odx_scene *proto_host, const double *rays_dev,
+                       int64_t n, odx_ray_record *records_dev, double *image_dev,
+                       void *stream);
+
+/*
+ * odx_render with HOST output buffers: copies the scene table in, renders into context
+ * buffers and copies records and image back to records_host / image_host (image_host may be
+ * NULL).  Synchronous.  Pinned host memory makes the copies faster.
+ */
+int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
+                        odx_ray_record *records_host, double *image_host);
+
+/* Read (stream-ordered, then synchronised) and optionally reset the device counters. */
+int32_t odx_get_stats(odx_ctx *ctx, void *stream, odx_stats *out, int32_t reset);
+
+/* Wait for `stream` with a deadline; ODX_ERR_TIMEOUT if it has not finished in timeout_s
+ * seconds (the work keeps running), ODX_ERR_DEVICE_FLAG if a kernel raised its flag. */
+int32_t odx_sync(odx_ctx *ctx, void *stream, double timeout_s);
+
+/*
+ * Emissivity normalisation of the analytic torus (host computation, no device work): the C
+ * for which a static path along the equator from r_+ to r_outer has optical depth 1 at
+ * frequency nu, i.e. C = 1 / int alpha_nu(r, pi/2)|_{C=1} dr (reading of "tau about 1 at the
+ * middle frequency").  Returns NaN for invalid arguments.
+ */
+double odx_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
+                      double r_outer);
+
+/*
+ * FMA-chain microbenchmark of the FP32 (precision = ODX_MIXED) or FP64 (ODX_FP64) vector
+ * pipe: writes the measured FLOP/s (FMA = 2 flops) of a full-device launch to *flops.
+ * Used as the denominator of the integrator's roofline.  Synchronous.
+ */
+int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ODYSSEY_H */

@@ -1,0 +1,241 @@
+// Device-side physics of the tracer: image-plane initial state, Kerr geodesic right-hand
+// side, thin-disk redshift and analytic-torus transfer coefficients (Pu et al. 2016,
+// Sections 2.1-2.3).  Written for the GB300 kernels; shares no code with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "odx_internal.h"
+
+namespace odx {
+
+constexpr double kSinFloor = 1e-8;  // Section 2.1: sin(theta) floored at 1e-8 near the poles
+constexpr int kFull = 0xffffffff;
+
+// Cash-Karp 4(5) tableau (Cash & Karp 1990), the adaptive fifth-order scheme of Section 2.1.
+#define CK_A21 (1.0 / 5.0)
+#define CK_A31 (3.0 / 40.0)
+#define CK_A32 (9.0 / 40.0)
+#define CK_A41 (3.0 / 10.0)
+#define CK_A42 (-9.0 / 10.0)
+#define CK_A43 (6.0 / 5.0)
+#define CK_A51 (-11.0 / 54.0)
+#define CK_A52 (5.0 / 2.0)
+#define CK_A53 (-70.0 / 27.0)
+#define CK_A54 (35.0 / 27.0)
+#define CK_A61 (1631.0 / 55296.0)
+#define CK_A62 (175.0 / 512.0)
+#define CK_A63 (575.0 / 13824.0)
+#define CK_A64 (44275.0 / 110592.0)
+#define CK_A65 (253.0 / 4096.0)
+#define CK_B1 (37.0 / 378.0)
+#define CK_B3 (250.0 / 621.0)
+#define CK_B4 (125.0 / 594.0)
+#define CK_B6 (512.0 / 1771.0)
+// fifth- minus fourth-order weights (the embedded error estimate)
+#define CK_E1 (37.0 / 378.0 - 2825.0 / 27648.0)
+#define CK_E3 (250.0 / 621.0 - 18575.0 / 48384.0)
+#define CK_E4 (125.0 / 594.0 - 13525.0 / 55296.0)
+#define CK_E5 (-277.0 / 14336.0)
+#define CK_E6 (512.0 / 1771.0 - 1.0 / 4.0)
+
+// Per-ray constants the right-hand side needs.
+template <typename T>
+struct Geo {
+    T a, L, sgn;  // spin, angular momentum (E = 1), +1 literal / -1 physical direction
+};
+
+// Geodesic right-hand side ds-form: sgn * (r', theta', phi', t', p_r', p_theta') from
+// Eqs. 4, 5, 12, 9, 14, 15 (E = 1, mu = 0).  The momentum equations carry the terms in
+// F = 2 Sigma H that make them exactly Hamilton's equations off the null cone (they vanish
+// on it); without them the constraint H = 0 is unstable on inward rays.
+template <typename T>
+__device__ __forceinline__ void geodesic_rhs(const Geo<T> &g, T r, T th, T pr, T pth, T f[6])
+{
+    T s, c;
+    if constexpr (sizeof(T) == 8) {
+        sincos(th, &s, &c);
+    } else {
+        __sincosf(th, &s, &c);
+    }
+    s = fmax(s, T(kSinFloor));
+    const T a = g.a, L = g.L;
+    const T r2 = r * r, a2 = a * a;
+    const T Sig = r2 + a2 * c * c;
+    const T Del = r2 - T(2) * r + a2;
+    const T iSD = T(1) / (Sig * Del);
+    const T iS = Del * iSD;
+    const T is = T(1) / s;
+    const T is2 = is * is;
+    const T rr = r2 + a2;
+    const T P = rr - a * L;
+    const T q = L * is - a * s;
+    const T pr2 = pr * pr, pth2 = pth * pth;
+    const T F = Del * pr2 + pth2 + q * q - P * P * (Sig * iSD);
+    const T kap = pth2 + L * L * is2 + a2 * s * s;
+    const T rm1 = r - T(1);
+    const T twor = T(2) * r;
+    f[0] = g.sgn * (Del * pr * iS);
+    f[1] = g.sgn * (pth * iS);
+    f[2] = g.sgn * ((twor * a + (Sig - twor) * L * is2) * iSD);
+    f[3] = g.sgn * (T(1) + (twor * rr - twor * a * L) * iSD);
+    f[4] = g.sgn * ((-kap * rm1 + twor * rr - T(2) * a * L) * iSD - T(2) * pr2 * rm1 * iS +
+                    F * (rm1 * iSD + r * iS * iS));
+    f[5] = g.sgn * (s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS);
+}
+
+// Outer horizon and ISCO radius (prograde for a >= 0) of a disk rotating in +phi
+// (Bardeen, Press & Teukolsky 1972, cited in Section 4.3).
+__device__ __forceinline__ double horizon_radius(double a) { return 1.0 + sqrt(1.0 - a * a); }
+
+__device__ __forceinline__ double isco_radius(double a)
+{
+    const double z1 = 1.0 + cbrt(1.0 - a * a) * (cbrt(1.0 + a) + cbrt(1.0 - a));
+    const double z2 = sqrt(3.0 * a * a + z1 * z1);
+    const double root = sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2));
+    return a >= 0.0 ? 3.0 + z2 - root : 3.0 + z2 + root;
+}
+
+// Eq. 2 for circular Keplerian orbits in the equatorial plane:
+// g = 1 / (u^t (1 - Omega L)), Omega = 1/(r^1.5 + a).
+__device__ __forceinline__ double disk_redshift(double a, double r, double L)
+{
+    const double rs = sqrt(r);
+    const double r15 = r * rs;
+    const double Om = 1.0 / (r15 + a);
+    const double ut = (r15 + a) / (sqrt(rs * r) * sqrt(r15 - 3.0 * rs + 2.0 * a));
+    return 1.0 / (ut * (1.0 - Om * L));
+}
+
+// Initial state of the ray through image-plane point (alpha, beta), Section 2.2:
+// Eqs. 18-19 (observer grid -> Cartesian), 20-22 (-> Boyer-Lindquist), 24-26 (velocity of a
+// ray perpendicular to the image plane), 7 (E, then scaled to 1), 8 (L), 4-5 (p_r, p_theta),
+// 13 (Q).  In the physical convention the traced (real) photon moves opposite to Eqs. 24-26.
+struct InitOut {
+    double y[6];
+    double L, Q;
+};
+
+__device__ __forceinline__ InitOut init_ray(double a, double r_obs, double theta_obs,
+                                            double phi_obs, double alpha, double beta,
+                                            double sgn)
+{
+    double sto, cto, spo, cpo;
+    sincos(theta_obs, &sto, &cto);
+    sincos(phi_obs, &spo, &cpo);
+    const double D = sqrt(r_obs * r_obs + a * a) * sto - beta * cto;
+    const double xp = D * cpo - alpha * spo;
+    const double yp = D * spo + alpha * cpo;
+    const double zp = r_obs * cto + beta * sto;
+    const double w = xp * xp + yp * yp + zp * zp - a * a;
+    const double r = sqrt(0.5 * (w + sqrt(w * w + 4.0 * a * a * zp * zp)));
+    const double th = acos(zp / r);
+    const double ph = atan2(yp, xp);
+    double s, c;
+    sincos(th, &s, &c);
+    s = fmax(s, kSinFloor);
+    const double R = sqrt(r * r + a * a);
+    double sP, cP;
+    sincos(ph - phi_obs, &sP, &cP);
+    const double Sig = r * r + a * a * c * c;
+    const double Del = r * r - 2.0 * r + a * a;
+    double rd = sgn * (-(r * R * s * sto * cP + R * R * c * cto) / Sig);
+    double td = sgn * ((r * s * cto - R * c * sto * cP) / Sig);
+    double pd = sgn * (sto * sP / (R * s));
+    const double E2 = ((Sig - 2.0 * r) / (Sig * Del)) * (Sig * rd * rd + Sig * Del * td * td) +
+                      Del * pd * pd * s * s;
+    const double iE = 1.0 / sqrt(E2);
+    rd *= iE;
+    td *= iE;
+    pd *= iE;
+    InitOut o;
+    o.L = (Sig * Del * pd - 2.0 * a * r) * s * s / (Sig - 2.0 * r);
+    o.y[0] = r;
+    o.y[1] = th;
+    o.y[2] = ph;
+    o.y[3] = 0.0;
+    o.y[4] = Sig * rd / Del;
+    o.y[5] = Sig * td;
+    o.Q = o.y[5] * o.y[5] + (o.L * o.L / (s * s) - a * a) * c * c;
+    return o;
+}
+
+// Relative null violation and relative Carter-constant drift at the end of a ray.
+__device__ __forceinline__ double null_violation(double a, double L, const double y[6])
+{
+    const double s = fmax(sin(y[1]), kSinFloor);
+    const double r = y[0];
+    const double Del = r * r - 2.0 * r + a * a;
+    const double t1 = Del * y[4] * y[4], t2 = y[5] * y[5];
+    const double q = L / s - a * s;
+    const double t3 = q * q;
+    const double P = r * r + a * a - a * L;
+    const double t4 = P * P / Del;
+    return (t1 + t2 + t3 - t4) / (fabs(t1) + t2 + t3 + fabs(t4));
+}
+
+__device__ __forceinline__ double carter_q(double a, double L, const double y[6])
+{
+    double s, c;
+    sincos(y[1], &s, &c);
+    s = fmax(s, kSinFloor);
+    return y[5] * y[5] + (L * L / (s * s) - a * a) * c * c;
+}
+
+// Analytic torus of the GRRT workload: Keplerian flow Omega = 1/(r^1.5 + a) where r >= r_ISCO
+// and the orbit is timelike at (r, theta), zero-angular-momentum observers elsewhere; thermal
+// emission j = C n_e^2 T^-1/2 exp(-nu0/T), Kirchhoff absorption alpha = j / B_nu(T) with
+// B_nu = 2 nu^3 / (exp(nu/T) - 1); nu0 = nu_obs / g.  Returns the transfer right-hand sides
+// of Eqs. 30-31: dtau/ds = alpha/g, dI/ds = j / (g nu0^3) exp(-tau).
+struct Medium {
+    double ne_index, inv_2w2, T0, T_index, C_norm, r_isco;
+    double freqs[ODX_MAX_FREQ];
+    int n_freq;
+};
+
+template <int NF>
+__device__ __forceinline__ void torus_rhs64(const Medium &m, double a, double L, double r,
+                                            double th, const double *tau, double *ftau,
+                                            double *fI)
+{
+    double s, c;
+    sincos(th, &s, &c);
+    s = fmax(s, kSinFloor);
+    const double r2 = r * r, a2 = a * a, s2 = s * s;
+    const double Sig = r2 + a2 * c * c;
+    const double Del = r2 - 2.0 * r + a2;
+    const double A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
+    const double iS = 1.0 / Sig;
+    const double gtt = -(1.0 - 2.0 * r * iS);
+    const double gtp = -2.0 * a * r * s2 * iS;
+    const double gpp = A * s2 * iS;
+    double Om = 1.0 / (r * sqrt(r) + a);
+    double N = gtt + 2.0 * gtp * Om + gpp * Om * Om;
+    if (!(r >= m.r_isco && N < 0.0)) {
+        Om = 2.0 * a * r / A;
+        N = gtt + 2.0 * gtp * Om + gpp * Om * Om;
+    }
+    const double ig = (1.0 - Om * L) / sqrt(-N);  // 1/g = u^t (1 - Omega L), Eq. 2
+    const double lr = log(r);
+    const double ne = exp(-m.ne_index * lr - c * c * m.inv_2w2);
+    const double iTe = exp(m.T_index * lr) / m.T0;
+    const double pref = m.C_norm * ne * ne * sqrt(iTe);  // C n_e^2 T^-1/2
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        if (k < m.n_freq) {
+            const double nu0 = m.freqs[k] * ig;
+            const double x = nu0 * iTe;
+            const double em = exp(-x);
+            const double om = (x > 0.5) ? 1.0 - em : -expm1(-x);  // 1 - exp(-nu0/T)
+            const double inu3 = 1.0 / (nu0 * nu0 * nu0);
+            ftau[k] = 0.5 * pref * om * inu3 * ig;            // Eq. 30
+            fI[k] = pref * em * inu3 * ig * exp(-tau[k]);     // Eq. 31
+        } else {
+            ftau[k] = 0.0;
+            fI[k] = 0.0;
+        }
+    }
+}
+
+}  // namespace odx

@@ -1,0 +1,449 @@
+// Host side of the C ABI declared in include/odyssey.h: context and scratch management,
+// argument validation, scene tables, launches, statistics and host-buffer rendering.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "odx_internal.h"
+
+namespace odx {
+cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                              int32_t num_sms, cudaStream_t st);
+cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                               int32_t num_sms, cudaStream_t st);
+}  // namespace odx
+
+using namespace odx;
+
+struct odx_ctx {
+    int device = 0;
+    int num_sms = 0;
+    odx_launch launch{128, 4, 32, 1};
+    unsigned long long *queue = nullptr;
+    DevStats *stats = nullptr;
+    DevScene *scenes = nullptr;
+    int64_t scene_cap = 0;
+    std::vector<DevScene> host_scenes;
+    // buffers of odx_render_host
+    cudaStream_t host_stream = nullptr;
+    void *hbuf = nullptr;
+    size_t hbuf_bytes = 0;
+    std::string last_error;
+};
+
+namespace {
+
+const char *kVersion = "odyssey-gb300 0.1 (sm_103a)";
+
+int32_t fail(odx_ctx *ctx, int32_t code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return code;
+}
+
+int32_t cuda_fail(odx_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, ODX_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define ODX_CUDA(ctx, call)                                            \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
+    } while (0)
+
+bool finite(double x) { return isfinite(x) != 0; }
+
+int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
+{
+    if (!finite(s.a) || fabs(s.a) >= 1.0) return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: |a| must be < 1", k);
+    const double rp = 1.0 + sqrt(1.0 - s.a * s.a);
+    if (!finite(s.r_obs) || s.r_obs <= 10.0 * rp)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: r_obs must exceed 10 r_+", k);
+    if (!list_mode && (!finite(s.theta_obs) || s.theta_obs < 0.0 || s.theta_obs > M_PI))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: theta_obs must lie in [0, pi]", k);
+    if (!finite(s.phi_obs)) return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: phi_obs not finite", k);
+    if (!list_mode) {
+        if (!finite(s.alpha_min) || !finite(s.alpha_max) || !(s.alpha_min < s.alpha_max) ||
+            !finite(s.beta_min) || !finite(s.beta_max) || !(s.beta_min < s.beta_max))
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: empty or non-finite window", k);
+        if (s.n_alpha < 1 || s.n_beta < 1)
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
+    }
+    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_TORUS)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown emitter %d", k, s.emitter);
+    if (s.emitter == ODX_EMIT_THIN_DISK &&
+        (!finite(s.r_in) || !finite(s.r_out) || !(s.r_out > 0.0) || !finite(s.q_emis)))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad thin-disk parameters", k);
+    if (s.emitter == ODX_EMIT_TORUS) {
+        if (s.n_freq < 1 || s.n_freq > ODX_MAX_FREQ)
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: n_freq must be 1..%d", k, ODX_MAX_FREQ);
+        for (int f = 0; f < s.n_freq; ++f)
+            if (!finite(s.freqs[f]) || !(s.freqs[f] > 0.0))
+                return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: frequencies must be > 0", k);
+        if (!finite(s.C_norm) || s.C_norm < 0.0 || !(s.theta_width > 0.0) || !(s.T0 > 0.0) ||
+            !finite(s.ne_index) || !finite(s.T_index) || !finite(s.theta_width) || !finite(s.T0))
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad torus parameters", k);
+    }
+    if (!(s.rtol > 0.0) || !finite(s.rtol) || !(s.h0 > 0.0) || !finite(s.h0) ||
+        !(s.hmax_frac > 0.0) || !finite(s.hmax_frac) || !(s.horizon_factor > 1.0) ||
+        !finite(s.horizon_factor) || s.max_steps < 1)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad integrator controls", k);
+    if (s.convention != ODX_CONV_PHYSICAL && s.convention != ODX_CONV_LITERAL)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown convention", k);
+    if (s.precision != ODX_FP64 && s.precision != ODX_MIXED)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown precision", k);
+    if (s.precision == ODX_MIXED &&
+        (!(s.rtol_fp32 > 0.0) || !finite(s.rtol_fp32) || !finite(s.r_switch) || s.r_switch < 0.0))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad mixed-precision controls", k);
+    if (s.reserved != 0) return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: reserved must be 0", k);
+    return ODX_OK;
+}
+
+int32_t nf_slots(int32_t emitter, int32_t n_freq)
+{
+    if (emitter != ODX_EMIT_TORUS) return 0;
+    return n_freq <= 4 ? 4 : 8;
+}
+
+int32_t ensure_scene_capacity(odx_ctx *ctx, int64_t n)
+{
+    if (n <= ctx->scene_cap) return ODX_OK;
+    if (ctx->scenes) ODX_CUDA(ctx, cudaFree(ctx->scenes));
+    ctx->scenes = nullptr;
+    ctx->scene_cap = 0;
+    const int64_t cap = n < 64 ? 64 : n;
+    ODX_CUDA(ctx, cudaMalloc(&ctx->scenes, cap * sizeof(DevScene)));
+    ctx->scene_cap = cap;
+    return ODX_OK;
+}
+
+int32_t set_device(odx_ctx *ctx)
+{
+    ODX_CUDA(ctx, cudaSetDevice(ctx->device));
+    return ODX_OK;
+}
+
+// Validate, build the scene table, copy it and launch.  Shared by the render and list paths.
+int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const double *rays,
+               int64_t n_list, odx_ray_record *records, double *image, cudaStream_t st,
+               int64_t *total_rays, int64_t *total_image)
+{
+    const bool list_mode = rays != nullptr || n_list >= 0;
+    if (!scenes || n_scenes < 1) return fail(ctx, ODX_ERR_INVALID_ARG, "no scenes");
+    if (!records) return fail(ctx, ODX_ERR_INVALID_ARG, "records pointer is NULL");
+    if (((uintptr_t)records & 15u) != 0)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "records must be 16-byte aligned");
+    if (image && ((uintptr_t)image & 7u) != 0)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "image must be 8-byte aligned");
+    for (int k = 0; k < n_scenes; ++k) {
+        int32_t rc = validate_scene(ctx, scenes[k], k, list_mode);
+        if (rc != ODX_OK) return rc;
+        if (scenes[k].emitter != scenes[0].emitter || scenes[k].precision != scenes[0].precision ||
+            (scenes[0].emitter == ODX_EMIT_TORUS && scenes[k].n_freq != scenes[0].n_freq))
+            return fail(ctx, ODX_ERR_INVALID_ARG,
+                        "scene %d: all scenes of one call must share emitter, precision, n_freq", k);
+    }
+    ctx->host_scenes.resize(n_scenes);
+    int64_t ray = 0, img = 0;
+    const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
+    for (int k = 0; k < n_scenes; ++k) {
+        DevScene &d = ctx->host_scenes[k];
+        memset(&d, 0, sizeof(d));
+        d.s = scenes[k];
+        d.ray_begin = ray;
+        d.n_rays = list_mode ? n_list : (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        d.img_offset = img;
+        ray += d.n_rays;
+        img += nf * d.n_rays;
+    }
+    if (total_rays) *total_rays = ray;
+    if (total_image) *total_image = img;
+    if (list_mode && n_list > 0 && !rays)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "rays pointer is NULL");
+    if (ray == 0) return ODX_OK;
+    int32_t rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    rc = ensure_scene_capacity(ctx, n_scenes);
+    if (rc != ODX_OK) return rc;
+    ODX_CUDA(ctx, cudaMemcpyAsync(ctx->scenes, ctx->host_scenes.data(),
+                                  n_scenes * sizeof(DevScene), cudaMemcpyHostToDevice, st));
+    ODX_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), st));
+    TraceArgs a{};
+    a.scenes = ctx->scenes;
+    a.n_scenes = n_scenes;
+    a.list_mode = list_mode ? 1 : 0;
+    a.rays = rays;
+    a.n_total = ray;
+    a.records = records;
+    a.image = image;
+    a.queue = ctx->queue;
+    a.stats = ctx->stats;
+    a.chunk = ctx->launch.chunk;
+    a.persistent = ctx->launch.persistent;
+    const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
+    cudaError_t e = scenes[0].precision == ODX_MIXED
+                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st)
+                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace kernel launch");
+    return ODX_OK;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *odx_version(void) { return kVersion; }
+
+const char *odx_error_string(int32_t code)
+{
+    switch (code) {
+    case ODX_OK: return "ok";
+    case ODX_ERR_INVALID_ARG: return "invalid argument";
+    case ODX_ERR_CUDA: return "CUDA error";
+    case ODX_ERR_TIMEOUT: return "timeout";
+    case ODX_ERR_DEVICE_FLAG: return "device error flag raised";
+    case ODX_ERR_NO_DEVICE: return "no suitable CUDA device";
+    case ODX_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown error code";
+    }
+}
+
+const char *odx_last_error(const odx_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int32_t odx_create(odx_ctx **out, int32_t device)
+{
+    if (!out) return ODX_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+        return ODX_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return ODX_ERR_NO_DEVICE;
+    if (prop.major != 10 || prop.minor != 3) return ODX_ERR_NO_DEVICE;
+    odx_ctx *ctx = new odx_ctx();
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->queue, 256) != cudaSuccess ||
+        cudaMalloc(&ctx->stats, sizeof(DevStats)) != cudaSuccess ||
+        cudaMemset(ctx->stats, 0, sizeof(DevStats)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        odx_destroy(ctx);
+        return ODX_ERR_CUDA;
+    }
+    *out = ctx;
+    return ODX_OK;
+}
+
+int32_t odx_destroy(odx_ctx *ctx)
+{
+    if (!ctx) return ODX_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->queue) cudaFree(ctx->queue);
+    if (ctx->stats) cudaFree(ctx->stats);
+    if (ctx->scenes) cudaFree(ctx->scenes);
+    if (ctx->hbuf) cudaFree(ctx->hbuf);
+    if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    delete ctx;
+    return ODX_OK;
+}
+
+int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *L)
+{
+    if (!ctx || !L) return ODX_ERR_INVALID_ARG;
+    if (L->block < 32 || L->block > 1024 || (L->block % 32) != 0)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "block must be a multiple of 32 in 32..1024");
+    if (L->blocks_per_sm < 1 || L->blocks_per_sm > 64)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "blocks_per_sm must be 1..64");
+    if (L->chunk < 1 || L->chunk > 4096) return fail(ctx, ODX_ERR_INVALID_ARG, "chunk must be 1..4096");
+    if (L->persistent != 0 && L->persistent != 1)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    ctx->launch = *L;
+    return ODX_OK;
+}
+
+int32_t odx_get_launch(const odx_ctx *ctx, odx_launch *L)
+{
+    if (!ctx || !L) return ODX_ERR_INVALID_ARG;
+    *L = ctx->launch;
+    return ODX_OK;
+}
+
+int32_t odx_render(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
+                   odx_ray_record *records, double *image, void *stream)
+{
+    if (!ctx) return ODX_ERR_INVALID_ARG;
+    return submit(ctx, scenes, n_scenes, nullptr, -1, records, image, (cudaStream_t)stream,
+                  nullptr, nullptr);
+}
+
+int32_t odx_trace_rays(odx_ctx *ctx, const odx_scene *proto, const double *rays, int64_t n,
+                       odx_ray_record *records, double *image, void *stream)
+{
+    if (!ctx) return ODX_ERR_INVALID_ARG;
+    if (n < 0) return fail(ctx, ODX_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return proto ? ODX_OK : fail(ctx, ODX_ERR_INVALID_ARG, "no prototype scene");
+    return submit(ctx, proto, 1, rays, n, records, image, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
+                        odx_ray_record *records_host, double *image_host)
+{
+    if (!ctx || !scenes || n_scenes < 1 || !records_host) return ODX_ERR_INVALID_ARG;
+    int64_t nr = 0, ni = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        if (scenes[k].n_alpha < 1 || scenes[k].n_beta < 1)
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
+        const int64_t p = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        nr += p;
+        ni += p * (scenes[k].emitter == ODX_EMIT_TORUS ? scenes[k].n_freq : 1);
+    }
+    const size_t rec_bytes = (size_t)nr * sizeof(odx_ray_record);
+    const size_t img_bytes = (size_t)ni * sizeof(double);
+    int32_t rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    if (ctx->hbuf_bytes < rec_bytes + img_bytes) {
+        if (ctx->hbuf) ODX_CUDA(ctx, cudaFree(ctx->hbuf));
+        ctx->hbuf = nullptr;
+        ctx->hbuf_bytes = 0;
+        ODX_CUDA(ctx, cudaMalloc(&ctx->hbuf, rec_bytes + img_bytes));
+        ctx->hbuf_bytes = rec_bytes + img_bytes;
+    }
+    odx_ray_record *rec = (odx_ray_record *)ctx->hbuf;
+    double *img = (double *)((char *)ctx->hbuf + rec_bytes);
+    rc = submit(ctx, scenes, n_scenes, nullptr, -1, rec, image_host ? img : nullptr,
+                ctx->host_stream, nullptr, nullptr);
+    if (rc != ODX_OK) return rc;
+    ODX_CUDA(ctx, cudaMemcpyAsync(records_host, rec, rec_bytes, cudaMemcpyDeviceToHost,
+                                  ctx->host_stream));
+    if (image_host)
+        ODX_CUDA(ctx, cudaMemcpyAsync(image_host, img, img_bytes, cudaMemcpyDeviceToHost,
+                                      ctx->host_stream));
+    ODX_CUDA(ctx, cudaStreamSynchronize(ctx->host_stream));
+    return ODX_OK;
+}
+
+int32_t odx_get_stats(odx_ctx *ctx, void *stream, odx_stats *out, int32_t reset)
+{
+    if (!ctx || !out) return ODX_ERR_INVALID_ARG;
+    int32_t rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    DevStats d;
+    cudaStream_t st = (cudaStream_t)stream;
+    ODX_CUDA(ctx, cudaMemcpyAsync(&d, ctx->stats, sizeof(d), cudaMemcpyDeviceToHost, st));
+    ODX_CUDA(ctx, cudaStreamSynchronize(st));
+    out->rays = (int64_t)d.rays;
+    out->steps_accepted = (int64_t)d.acc;
+    out->steps_rejected = (int64_t)d.rej;
+    out->steps_fp64 = (int64_t)d.fp64;
+    out->lane_slots = (int64_t)d.slots;
+    out->lane_active = (int64_t)d.active;
+    out->error_flag = d.error_flag;
+    out->reserved = 0;
+    if (reset) {
+        ODX_CUDA(ctx, cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), st));
+        ODX_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    return ODX_OK;
+}
+
+int32_t odx_sync(odx_ctx *ctx, void *stream, double timeout_s)
+{
+    if (!ctx || !(timeout_s >= 0.0)) return ODX_ERR_INVALID_ARG;
+    int32_t rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaStreamQuery");
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(ctx, ODX_ERR_TIMEOUT, "stream not done after %.3f s", el);
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    int32_t flag = 0;
+    ODX_CUDA(ctx, cudaMemcpy(&flag, &ctx->stats->error_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) return fail(ctx, ODX_ERR_DEVICE_FLAG, "device error flag %d", flag);
+    return ODX_OK;
+}
+
+double odx_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
+                      double r_outer)
+{
+    if (!isfinite(a) || fabs(a) >= 1.0 || !(nu > 0.0) || !(T0 > 0.0) || !isfinite(ne_index) ||
+        !isfinite(T_index) || !isfinite(r_outer))
+        return NAN;
+    const double rp = 1.0 + sqrt(1.0 - a * a);
+    if (!(r_outer > rp)) return NAN;
+    // alpha_nu along the static equatorial path with C = 1, integrated in u = ln r with
+    // 16-point Gauss-Legendre on 512 equal panels
+    std::vector<double> x, w;
+    gauss_legendre(16, x, w);
+    const double u0 = log(rp), u1 = log(r_outer);
+    const int panels = 512;
+    const double du = (u1 - u0) / panels;
+    double sum = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        const double mid = u0 + (p + 0.5) * du;
+        for (int i = 0; i < 16; ++i) {
+            const double r = exp(mid + 0.5 * du * x[i]);
+            const double ne = exp(-ne_index * log(r));
+            const double T = T0 * exp(-T_index * log(r));
+            const double alpha = ne * ne / sqrt(T) * (-expm1(-nu / T)) / (2.0 * nu * nu * nu);
+            sum += 0.5 * du * w[i] * alpha * r;
+        }
+    }
+    return 1.0 / sum;
+}
+
+int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops)
+{
+    if (!ctx || !flops || (precision != ODX_FP64 && precision != ODX_MIXED))
+        return ODX_ERR_INVALID_ARG;
+    int32_t rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    cudaError_t e = run_fma_peak(precision, ctx->num_sms, flops);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fma peak");
+    return ODX_OK;
+}
+
+}  // extern "C"

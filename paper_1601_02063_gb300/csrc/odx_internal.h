@@ -1,0 +1,51 @@
+// Internal declarations shared by the host API (odx_api.cu) and the kernel translation
+// units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/odyssey.h"
+
+namespace odx {
+
+// A scene as the kernels read it: the caller's description plus where its rays sit in the
+// launch-wide ray numbering and where its image planes start.
+struct DevScene {
+    odx_scene s;
+    int64_t ray_begin;  // first global ray index of this scene
+    int64_t n_rays;     // n_alpha * n_beta (list mode: n)
+    int64_t img_offset; // offset of this scene's image planes, in doubles
+    int64_t pad;
+};
+
+// Device counters; 64-bit for atomicAdd.
+struct DevStats {
+    unsigned long long rays, acc, rej, fp64, slots, active;
+    int32_t error_flag;
+    int32_t pad;
+};
+
+struct TraceArgs {
+    const DevScene *scenes;
+    int32_t n_scenes;
+    int32_t list_mode;     // 1: rays[n][4] = (alpha, beta, a, cos i) with scene 0 as prototype
+    const double *rays;
+    int64_t n_total;
+    odx_ray_record *records;
+    double *image;         // may be null
+    unsigned long long *queue;
+    DevStats *stats;
+    int32_t chunk;
+    int32_t persistent;
+};
+
+// Launch the tracing kernel matching (emitter, n_freq, precision) on `stream`.
+cudaError_t launch_trace(const TraceArgs &args, int32_t emitter, int32_t n_freq,
+                         int32_t precision, const odx_launch &launch, int32_t num_sms,
+                         cudaStream_t stream);
+
+// FMA-chain peak microbenchmark: returns flop/s via *flops (synchronous).
+cudaError_t run_fma_peak(int32_t precision, int32_t num_sms, double *flops);
+
+}  // namespace odx

@@ -1,0 +1,150 @@
+// Pieces shared by the tracing kernels: the warp-level ray queue, scene lookup, ray inputs,
+// vectorised record stores and statistics.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kerr_device.cuh"
+#include "odx_internal.h"
+
+namespace odx {
+
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ULL); }
+
+// Warp-uniform pool of ray indices [next, end) taken from the global queue.  In the
+// non-persistent launch every thread owns the single ray with its global thread index.
+struct WarpQueue {
+    long long next, end;
+    bool exhausted;
+
+    __device__ __forceinline__ void init(const TraceArgs &)
+    {
+        next = end = 0;
+        exhausted = false;
+    }
+
+    // Called by all 32 lanes together.  Lanes with live == false receive a ray index in id
+    // (or keep -1 when the queue is drained).
+    __device__ __forceinline__ void refill(const TraceArgs &A, int lane, bool live, int64_t &id)
+    {
+        id = -1;
+        if (exhausted) return;
+        if (!A.persistent) {
+            const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+            if (!live && t < A.n_total) id = t;
+            exhausted = true;
+            return;
+        }
+        unsigned need = __ballot_sync(kFull, !live);
+        // each pass either hands out rays or takes a new chunk; bounded by 32 lanes + 1
+        for (int pass = 0; need != 0u && pass < 66; ++pass) {
+            if (next >= end) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)A.chunk);
+                base = __shfl_sync(kFull, base, 0);
+                if ((long long)base >= A.n_total) {
+                    exhausted = true;
+                    break;
+                }
+                next = (long long)base;
+                end = min((long long)base + A.chunk, (long long)A.n_total);
+            }
+            const int take = (int)min((long long)__popc(need), end - next);
+            const unsigned below = (lane == 0) ? 0u : (0xffffffffu >> (32 - lane));
+            const int rank = __popc(need & below);
+            if (((need >> lane) & 1u) && rank < take) id = next + rank;
+            next += take;
+            need &= ~__ballot_sync(kFull, id >= 0);
+        }
+    }
+};
+
+__device__ __forceinline__ int32_t find_scene(const TraceArgs &A, int64_t id)
+{
+    if (A.list_mode || A.n_scenes == 1) return 0;
+    int lo = 0, hi = A.n_scenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.scenes[mid].ray_begin <= id)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Image-plane coordinates and per-ray (a, theta_obs).  Pixel centres:
+// alpha_i = alpha_min + (i + 1/2)(alpha_max - alpha_min)/n_alpha.
+__device__ __forceinline__ void ray_inputs(const TraceArgs &A, const DevScene &S, int64_t id,
+                                           double &alpha, double &beta, double &a,
+                                           double &theta_obs)
+{
+    if (A.list_mode) {
+        const double *p = A.rays + 4 * id;
+        alpha = p[0];
+        beta = p[1];
+        a = p[2];
+        theta_obs = acos(p[3]);
+    } else {
+        const int64_t local = id - S.ray_begin;
+        const int64_t i = local % S.s.n_alpha, j = local / S.s.n_alpha;
+        alpha = S.s.alpha_min + (((double)i + 0.5) * (S.s.alpha_max - S.s.alpha_min)) / S.s.n_alpha;
+        beta = S.s.beta_min + (((double)j + 0.5) * (S.s.beta_max - S.s.beta_min)) / S.s.n_beta;
+        a = S.s.a;
+        theta_obs = S.s.theta_obs;
+    }
+}
+
+struct RecordOut {
+    int32_t status, n_acc, n_rej, n_cross;
+    double r_cross, phi_cross, r_hit, phi_hit, g, intensity, H_end, Q_drift;
+};
+
+// One 80-byte record as five 16-byte stores (every sector written in full).
+__device__ __forceinline__ void store_record(odx_ray_record *dst, const RecordOut &o)
+{
+    int4 *w = reinterpret_cast<int4 *>(dst);
+    w[0] = make_int4(o.status, o.n_acc, o.n_rej, o.n_cross);
+    double2 *d = reinterpret_cast<double2 *>(w + 1);
+    d[0] = make_double2(o.r_cross, o.phi_cross);
+    d[1] = make_double2(o.r_hit, o.phi_hit);
+    d[2] = make_double2(o.g, o.intensity);
+    d[3] = make_double2(o.H_end, o.Q_drift);
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void flush_stats(const TraceArgs &A, int lane, unsigned long long rays,
+                                            unsigned long long acc, unsigned long long rej,
+                                            unsigned long long fp64, unsigned long long slots,
+                                            unsigned long long active)
+{
+    rays = warp_sum(rays);
+    acc = warp_sum(acc);
+    rej = warp_sum(rej);
+    fp64 = warp_sum(fp64);
+    slots = warp_sum(slots);
+    active = warp_sum(active);
+    if (lane == 0) {
+        atomicAdd(&A.stats->rays, rays);
+        atomicAdd(&A.stats->acc, acc);
+        atomicAdd(&A.stats->rej, rej);
+        atomicAdd(&A.stats->fp64, fp64);
+        atomicAdd(&A.stats->slots, slots);
+        atomicAdd(&A.stats->active, active);
+    }
+}
+
+inline dim3 trace_grid(const TraceArgs &A, const odx_launch &L, int32_t num_sms)
+{
+    if (L.persistent) return dim3((unsigned)(num_sms * L.blocks_per_sm));
+    const long long nb = (A.n_total + L.block - 1) / L.block;
+    return dim3((unsigned)(nb > 0 ? nb : 1));
+}
+
+}  // namespace odx

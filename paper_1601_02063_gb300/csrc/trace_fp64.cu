@@ -1,0 +1,356 @@
+// FP64 backward ray tracer for GB300 (sm_103a): persistent warps that refill finished lanes
+// from a global ray queue, one ray per lane, the whole Runge-Kutta state in registers.
+//
+// Per lane, one loop iteration is exactly one Cash-Karp attempt (Section 2.1: fifth-order
+// Runge-Kutta with adaptive step size), so a rejected step costs its lane one iteration and
+// never holds the other 31 lanes of the warp in a retry loop.  After an accepted step the
+// lane runs the event checks (equatorial crossing, horizon, escape) and evaluates the
+// right-hand side at the new point, which is both the escape test's dr/ds and the first
+// stage of the next step.  Finished lanes are refilled between iterations: a ballot finds
+// them, one lane takes `chunk` ray indices from the queue with a single atomicAdd, and the
+// indices are handed out by rank within the ballot.
+//
+// Radiative transfer (Section 2.3, Eqs. 30-31) rides on the same stages as extra
+// components: the optical depth tau_k needs its stage values (dI/ds depends on exp(-tau)),
+// the invariant intensity only its weighted sum, so only tau keeps per-stage slopes.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kerr_device.cuh"
+#include "odx_internal.h"
+#include "trace_common.cuh"
+
+namespace odx {
+
+template <int NF>
+struct Ray64 {
+    double y[6];      // r, theta, phi, t, p_r, p_theta
+    double k1[6];     // dy/ds at y (first Cash-Karp stage)
+    double tau[NF + 1], I[NF + 1], kt1[NF + 1], kI1[NF + 1];
+    double h, hs;     // next step; step used for the error scale of the current step
+    double a, L, Q0, sgn;
+    double r_start, r_stop, r_in, r_out;
+    double r_cross, phi_cross;
+    int64_t id;
+    int32_t scene, n_acc, n_rej, n_cross;
+};
+
+template <int NF>
+__device__ __forceinline__ void derivs64(const Geo<double> &g, const Medium &m, const double y[6],
+                                         const double *tau, double f[6], double *ft, double *fI)
+{
+    geodesic_rhs<double>(g, y[0], y[1], y[4], y[5], f);
+    if constexpr (NF > 0) torus_rhs64<NF>(m, g.a, g.L, y[0], y[1], tau, ft, fI);
+}
+
+// One Cash-Karp attempt of size h from (y, tau, I) with first stage (k1, kt1, kI1):
+// fifth-order geodesic y5, embedded error estimate e (geodesic components), and the
+// fifth-order transfer increments dtau, dI.
+template <int NF>
+__device__ __forceinline__ void ck_attempt64(const Geo<double> &g, const Medium &m,
+                                             const double y[6], const double k1[6],
+                                             const double *tau, const double *kt1,
+                                             const double *kI1, double h, double y5[6],
+                                             double e[6], double *dtau, double *dI)
+{
+    constexpr int N = NF + 1;
+    double k2[6], k3[6], k4[6], k5[6], k6[6], yt[6];
+    double t2[N], t3[N], t4[N], t5[N], t6[N], tt[N], fI[N], sI[N];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] = CK_B1 * kI1[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (CK_A21 * k1[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (CK_A21 * kt1[k]);
+    derivs64<NF>(g, m, yt, tt, k2, t2, fI);
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (CK_A31 * k1[i] + CK_A32 * k2[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (CK_A31 * kt1[k] + CK_A32 * t2[k]);
+    derivs64<NF>(g, m, yt, tt, k3, t3, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += CK_B3 * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (CK_A41 * k1[i] + CK_A42 * k2[i] + CK_A43 * k3[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (CK_A41 * kt1[k] + CK_A42 * t2[k] + CK_A43 * t3[k]);
+    derivs64<NF>(g, m, yt, tt, k4, t4, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += CK_B4 * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (CK_A51 * k1[i] + CK_A52 * k2[i] + CK_A53 * k3[i] + CK_A54 * k4[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (CK_A51 * kt1[k] + CK_A52 * t2[k] + CK_A53 * t3[k] + CK_A54 * t4[k]);
+    derivs64<NF>(g, m, yt, tt, k5, t5, fI);
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (CK_A61 * k1[i] + CK_A62 * k2[i] + CK_A63 * k3[i] + CK_A64 * k4[i] +
+                            CK_A65 * k5[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (CK_A61 * kt1[k] + CK_A62 * t2[k] + CK_A63 * t3[k] +
+                              CK_A64 * t4[k] + CK_A65 * t5[k]);
+    derivs64<NF>(g, m, yt, tt, k6, t6, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += CK_B6 * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        y5[i] = y[i] + h * (CK_B1 * k1[i] + CK_B3 * k3[i] + CK_B4 * k4[i] + CK_B6 * k6[i]);
+        e[i] = h * (CK_E1 * k1[i] + CK_E3 * k3[i] + CK_E4 * k4[i] + CK_E5 * k5[i] +
+                    CK_E6 * k6[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dtau[k] = h * (CK_B1 * kt1[k] + CK_B3 * t3[k] + CK_B4 * t4[k] + CK_B6 * t6[k]);
+        dI[k] = h * sI[k];
+    }
+}
+
+// Geodesic-only Cash-Karp step (fifth-order result), used to localise equatorial crossings.
+__device__ __noinline__ void ck_geo64(const Geo<double> &g, const double y[6], const double k1[6],
+                                      double h, double y5[6])
+{
+    const Medium m{};
+    double e[6], z[1] = {0.0}, d1[1], d2[1];
+    ck_attempt64<0>(g, m, y, k1, z, z, z, h, y5, e, d1, d2);
+}
+
+// Equatorial crossing inside an accepted step: solve cos(theta(sigma)) = 0 for the
+// fifth-order step of size sigma from the step start by Newton's method
+// (d cos(theta)/ds = -sin(theta) dtheta/ds), kept in the sign bracket by bisection, to
+// |cos(theta)| <= 1e-14 or 60 iterations.
+__device__ __noinline__ void locate_crossing64(const Geo<double> &g, const double y[6],
+                                               const double k1[6], double h, double yc[6])
+{
+    double lo = 0.0, hi = h;
+    double flo = cos(y[1]);
+    double y5[6];
+    ck_geo64(g, y, k1, h, y5);
+    const double fhi = cos(y5[1]);
+    double sig = lo - flo * (hi - lo) / (fhi - flo);
+    if (!(sig > lo && sig < hi)) sig = 0.5 * (lo + hi);
+    for (int it = 0; it < 60; ++it) {
+        ck_geo64(g, y, k1, sig, y5);
+        double sn, F;
+        sincos(y5[1], &sn, &F);
+        if (fabs(F) <= 1e-14) break;
+        if ((F > 0.0) == (flo > 0.0)) {
+            lo = sig;
+            flo = F;
+        } else {
+            hi = sig;
+        }
+        double f[6];
+        geodesic_rhs<double>(g, y5[0], y5[1], y5[4], y5[5], f);
+        const double dF = -sn * f[1];
+        double nx = sig - F / dF;
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (hi - lo <= 1e-15 * h) break;
+        sig = nx;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yc[i] = y5[i];
+}
+
+template <int NF>
+__device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScene &S,
+                                               const Ray64<NF> &R, int32_t status,
+                                               const double yend[6], double r_hit,
+                                               double phi_hit, double g, double inten)
+{
+    RecordOut o;
+    o.status = status;
+    o.n_acc = R.n_acc;
+    o.n_rej = R.n_rej;
+    o.n_cross = R.n_cross;
+    o.r_cross = R.r_cross;
+    o.phi_cross = R.phi_cross;
+    o.r_hit = r_hit;
+    o.phi_hit = phi_hit;
+    o.g = g;
+    o.intensity = inten;
+    o.H_end = null_violation(R.a, R.L, yend);
+    o.Q_drift = (carter_q(R.a, R.L, yend) - R.Q0) / fmax(fabs(R.Q0), 1.0);
+    store_record(A.records + R.id, o);
+    if (A.image) {
+        double *img = A.image + S.img_offset + (R.id - S.ray_begin);
+        if constexpr (NF > 0) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                if (k < S.s.n_freq) {
+                    const double nu = S.s.freqs[k];
+                    img[(int64_t)k * S.n_rays] = nu * nu * nu * R.I[k];
+                }
+            }
+        } else {
+            img[0] = inten;
+        }
+    }
+}
+
+__device__ __forceinline__ void load_medium(const DevScene &S, double a, Medium &m)
+{
+    m.ne_index = S.s.ne_index;
+    m.inv_2w2 = 1.0 / (2.0 * S.s.theta_width * S.s.theta_width);
+    m.T0 = S.s.T0;
+    m.T_index = S.s.T_index;
+    m.C_norm = S.s.C_norm;
+    m.r_isco = isco_radius(a);
+    m.n_freq = S.s.n_freq;
+#pragma unroll
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = S.s.freqs[k];
+}
+
+template <int NF>
+__global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    Ray64<NF> R;
+    Medium m{};
+    bool live = false;
+    WarpQueue q;
+    q.init(A);
+
+    unsigned long long my_slots = 0, my_active = 0;
+    unsigned long long my_rays = 0, my_acc = 0, my_rej = 0;
+
+    for (;;) {
+        // ---- refill finished lanes from the queue (all 32 lanes together) ------------------
+        int64_t id;
+        q.refill(A, lane, live, id);
+        if (id >= 0) {
+            const int32_t sidx = find_scene(A, id);
+            const DevScene &S = A.scenes[sidx];
+            double alpha, beta, a, theta_obs;
+            ray_inputs(A, S, id, alpha, beta, a, theta_obs);
+            R.id = id;
+            R.scene = sidx;
+            R.a = a;
+            R.sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
+            const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, R.sgn);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) R.y[i] = io.y[i];
+            R.L = io.L;
+            R.Q0 = io.Q;
+            R.r_start = io.y[0];
+            R.r_stop = S.s.horizon_factor * horizon_radius(a);
+            R.r_in = (S.s.r_in > 0.0) ? S.s.r_in : isco_radius(a);
+            R.r_out = S.s.r_out;
+            R.r_cross = qnan();
+            R.phi_cross = qnan();
+            R.n_acc = R.n_rej = R.n_cross = 0;
+#pragma unroll
+            for (int k = 0; k < NF + 1; ++k) R.tau[k] = R.I[k] = 0.0;
+            if constexpr (NF > 0) load_medium(S, a, m);
+            const Geo<double> g{R.a, R.L, R.sgn};
+            derivs64<NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+            R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);
+            R.hs = R.h;
+            live = true;
+        }
+        const unsigned act = __ballot_sync(kFull, live);
+        if (act == 0u) break;
+        if (lane == 0) {
+            my_slots += 32;
+            my_active += __popc(act);
+        }
+
+        if (live) {
+            // ---- one Cash-Karp attempt ----------------------------------------------------------
+            const DevScene &S = A.scenes[R.scene];
+            const Geo<double> g{R.a, R.L, R.sgn};
+            double y5[6], e[6], dtau[NF + 1], dI[NF + 1];
+            const double h = R.h;
+            ck_attempt64<NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, y5, e, dtau, dI);
+            double errmax = 0.0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const double sc = fabs(R.y[i]) + fabs(R.hs * R.k1[i]) + 1e-30;
+                errmax = fmax(errmax, fabs(e[i] / sc));
+            }
+            errmax /= S.s.rtol;
+            if (isnan(errmax)) errmax = INFINITY;
+
+            int32_t status = ODX_RUNNING;
+            if (errmax <= 1.0) {
+                ++R.n_acc;
+                const double h_next = (errmax > 1.89e-4) ? 0.9 * h * pow(errmax, -0.2) : 5.0 * h;
+                if ((cos(R.y[1]) > 0.0) != (cos(y5[1]) > 0.0)) {  // equatorial crossing
+                    double yc[6];
+                    locate_crossing64(g, R.y, R.k1, h, yc);
+                    ++R.n_cross;
+                    if (R.n_cross == 1) {
+                        R.r_cross = yc[0];
+                        R.phi_cross = yc[2];
+                    }
+                    if (S.s.emitter == ODX_EMIT_THIN_DISK && yc[0] >= R.r_in &&
+                        yc[0] <= R.r_out) {
+                        const double gz = disk_redshift(R.a, yc[0], R.L);
+                        const double g2 = gz * gz;
+                        const double inten = g2 * g2 * pow(yc[0], -S.s.q_emis);
+                        write_result64<NF>(A, S, R, ODX_DISK_HIT, yc, yc[0], yc[2], gz, inten);
+                        status = ODX_DISK_HIT;
+                    }
+                }
+                if (status == ODX_RUNNING) {
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) R.y[i] = y5[i];
+#pragma unroll
+                    for (int k = 0; k < NF; ++k) {
+                        R.tau[k] += dtau[k];
+                        R.I[k] += dI[k];
+                    }
+                    if (R.y[0] < R.r_stop) {
+                        status = ODX_CAPTURED;
+                    } else {
+                        derivs64<NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+                        if (R.k1[0] > 0.0 && R.y[0] > R.r_start) status = ODX_ESCAPED;
+                    }
+                    R.h = fmin(h_next, S.s.hmax_frac * R.y[0]);
+                    R.hs = R.h;
+                }
+            } else {
+                ++R.n_rej;
+                R.h = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);
+                if (R.h < 1e-12) status = ODX_NUMERR;
+            }
+            if (status == ODX_RUNNING && R.n_acc + R.n_rej >= S.s.max_steps)
+                status = ODX_MAXSTEPS;
+            if (status != ODX_RUNNING) {
+                if (status != ODX_DISK_HIT)
+                    write_result64<NF>(A, S, R, status, R.y, qnan(), qnan(), qnan(), 0.0);
+                my_rays += 1;
+                my_acc += R.n_acc;
+                my_rej += R.n_rej;
+                live = false;
+            }
+        }
+    }
+    flush_stats(A, lane, my_rays, my_acc, my_rej, 0ull, my_slots, my_active);
+}
+
+cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                              int32_t num_sms, cudaStream_t st)
+{
+    const dim3 block(L.block);
+    const dim3 grid = trace_grid(args, L, num_sms);
+    switch (nf_slots) {
+    case 0: trace_fp64_kernel<0><<<grid, block, 0, st>>>(args); break;
+    case 4: trace_fp64_kernel<4><<<grid, block, 0, st>>>(args); break;
+    case 8: trace_fp64_kernel<8><<<grid, block, 0, st>>>(args); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace odx
