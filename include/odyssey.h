@@ -38,6 +38,7 @@ extern "C" {
 #define ODX_ERR_DEVICE_FLAG 4 /* a kernel raised its device error flag (see odx_stats) */
 #define ODX_ERR_NO_DEVICE 5
 #define ODX_ERR_UNSUPPORTED 6
+#define ODX_ERR_TOO_LARGE 7 /* request exceeds a fixed capacity (odx_render_static) */
 
 /* ray status written to odx_ray_record.status */
 #define ODX_RUNNING 0
@@ -209,6 +210,33 @@ double odx_torus_norm(double a, double nu, double ne_index, double T0, double T_
  * Used as the denominator of the integrator's roofline.  Synchronous.
  */
 int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops);
+
+/*
+ * odx_render without any device allocation, for callers that must not call cudaMalloc:
+ * code whose device memory is owned entirely by another allocator (a framework's caching
+ * pool, or a fixed budget reserved at start-up) and which must not allocate behind that
+ * allocator's back, such as a renderer embedded as a plug-in in a host application or a
+ * serving loop that forbids allocation after warm-up.  The paper has no counterpart; this
+ * is a deployment variant of odx_render.
+ *
+ * The ray queue counter, the device statistics and the scene table live in one file-scope
+ * device array of 20,480 bytes that every GPU loading this library holds until the process
+ * exits; at most ODX_STATIC_MAX_SCENES scenes per call (more: ODX_ERR_TOO_LARGE, nothing
+ * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
+ * as odx_render) and the scene descriptions in host memory.  The call works on the calling
+ * thread's current device.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  The call allocates no device memory and frees none, and copies the scene table
+ * into the array with a stream-ordered copy.
+ *
+ * Every call shares the one array, which keeps the previous call's contents (the counter is
+ * cleared on each call): calls whose work overlaps on the GPU (on different streams, or
+ * from different threads without ordering) race and give wrong results; order them on one
+ * stream.  Same argument checks and return codes as odx_render, without odx_last_error text.
+ */
+#define ODX_STATIC_MAX_SCENES 64
+int32_t odx_render_static(const odx_scene *scenes_host, int32_t n_scenes,
+                          odx_ray_record *records_dev, double *image_dev, void *stream);
 
 #ifdef __cplusplus
 }

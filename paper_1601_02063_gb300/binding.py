@@ -15,8 +15,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libodyssey_gb300.so")
 MAX_FREQ = 8
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_FLAG, ERR_NO_DEVICE, ERR_UNSUPPORTED = \
-    range(7)
+(OK, ERR_INVALID_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE_FLAG, ERR_NO_DEVICE, ERR_UNSUPPORTED,
+ ERR_TOO_LARGE) = range(8)
+STATIC_MAX_SCENES = 64
 RUNNING, ESCAPED, CAPTURED, DISK_HIT, MAXSTEPS, NUMERR = range(6)
 EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
@@ -92,6 +93,7 @@ _SIGNATURES = [
     ("odx_sync", C.c_int32, [_P, _P, C.c_double]),
     ("odx_torus_norm", C.c_double, [C.c_double] * 6),
     ("odx_fma_peak", C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double)]),
+    ("odx_render_static", C.c_int32, [C.POINTER(odx_scene), C.c_int32, _P, _P, _P]),
 ]
 SYMBOLS = [s[0] for s in _SIGNATURES]
 
@@ -203,6 +205,14 @@ def odx_fma_peak(ctx, precision: str) -> float:
     v = C.c_double()
     _check(ctx, lib().odx_fma_peak(ctx, PRECISIONS[precision], C.byref(v)), "odx_fma_peak")
     return v.value
+
+
+def odx_render_static(scenes, records_ptr: int, image_ptr: int | None,
+                      stream: int | None = None) -> int:
+    """Render without any device allocation by the library (fixed static scratch); returns
+    the status code (no context, so no error text)."""
+    arr = scene_array(scenes)
+    return lib().odx_render_static(arr, len(arr), records_ptr, image_ptr or None, stream or None)
 
 
 # ---- marshalling helpers ----------------------------------------------------------------------

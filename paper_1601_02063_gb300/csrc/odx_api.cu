@@ -229,6 +229,24 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 
 }  // namespace
 
+namespace odx {
+// Argument checks of odx_render for callers without a context (no message is stored).
+int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes)
+{
+    if (!scenes || n_scenes < 1) return ODX_ERR_INVALID_ARG;
+    for (int k = 0; k < n_scenes; ++k) {
+        const int32_t rc = validate_scene(nullptr, scenes[k], k, false);
+        if (rc != ODX_OK) return rc;
+        if (scenes[k].emitter != scenes[0].emitter || scenes[k].precision != scenes[0].precision ||
+            (scenes[0].emitter == ODX_EMIT_TORUS && scenes[k].n_freq != scenes[0].n_freq))
+            return ODX_ERR_INVALID_ARG;
+    }
+    return ODX_OK;
+}
+
+int32_t transfer_slots(int32_t emitter, int32_t n_freq) { return nf_slots(emitter, n_freq); }
+}  // namespace odx
+
 extern "C" {
 
 const char *odx_version(void) { return kVersion; }
@@ -243,6 +261,7 @@ const char *odx_error_string(int32_t code)
     case ODX_ERR_DEVICE_FLAG: return "device error flag raised";
     case ODX_ERR_NO_DEVICE: return "no suitable CUDA device";
     case ODX_ERR_UNSUPPORTED: return "unsupported";
+    case ODX_ERR_TOO_LARGE: return "request exceeds the fixed static scratch capacity";
     default: return "unknown error code";
     }
 }
