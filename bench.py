@@ -262,6 +262,43 @@ def run_ours(args):
     achieved = flops / (sum(times) * 1e-3)
     traffic = read_traffic(WORKLOAD if args.size == 512 else None, args.precision)
 
+    # the plain FP64 path on the same image: its speed, and the production path's image
+    # error against it (the metric's accuracy condition)
+    fp64_info = None
+    if args.precision != "fp64":
+        sc64 = dict(scene, precision="fp64")
+        rec64, img64 = tr.alloc(n, B.n_image(scene))
+        tr.render(sc64, out=(rec64, img64))
+        torch.cuda.synchronize()
+        tr.stats(reset=True)
+        t64 = []
+        for _ in range(max(1, args.fp64_steps)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tr.render(sc64, out=(rec64, img64), stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        st64 = tr.stats(reset=True)
+        tr.render(scene, out=(rec, img))
+        torch.cuda.synchronize()
+        nimg = B.n_image(scene)
+        planes = B.image_planes(scene)
+        a = img[:nimg].view(planes, n).double()
+        b = img64[:nimg].view(planes, n).double()
+        errs = ((a - b).abs().sum(dim=1) / b.abs().sum(dim=1)).tolist()
+        steps64 = st64["steps_accepted"] + st64["steps_rejected"]
+        fp64_info = {"ns_per_photon_step": sum(t64) * 1e6 / steps64,
+                     "ms_per_image": statistics.mean(t64),
+                     "images_per_s": 1e3 / statistics.mean(t64),
+                     "steps_per_photon": steps64 / st64["rays"]}
+        image_error = errs
+        del rec64, img64
+    else:
+        image_error = [0.0] * B.image_planes(scene)
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     rec_h = torch.empty(n * B.RECORD_BYTES // 8, dtype=torch.float64).pin_memory().numpy()
     img_h = torch.empty(B.n_image(scene), dtype=torch.float64).pin_memory().numpy()
@@ -299,6 +336,9 @@ def run_ours(args):
                    "launch": B.odx_get_launch(tr.ctx)},
         "images_per_s": 1e3 / ms_per_step * world,
         "steps_per_photon": steps_all / rays_all,
+        "image_error_vs_fp64": image_error,
+        "fp64_path": fp64_info,
+        "fp64_step_fraction": st["steps_fp64"] / max(1, steps_local),
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -324,7 +364,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed renders of the plain FP64 path beside the production path")
     ap.add_argument("--size", type=int, default=512,
                     help="image side (the workload is 512; smaller sizes are for profiling)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")

@@ -117,6 +117,8 @@ typedef struct odx_launch {
     int32_t chunk;         /* rays a warp takes from the global queue at a time    */
     int32_t persistent;    /* 1: persistent warps refilling lanes from the queue;
                               0: one ray per thread, no queue                       */
+    int32_t fp64_batch;    /* ODX_MIXED: a warp runs an FP64 step once this many of
+                              its lanes wait for one (or no FP32 lane is left), 1..32 */
 } odx_launch;
 
 /* Counters accumulated on the device by every tracing launch since the last reset. */

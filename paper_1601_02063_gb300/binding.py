@@ -56,7 +56,7 @@ class odx_ray_record(C.Structure):
 
 class odx_launch(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk", C.c_int32),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32), ("fp64_batch", C.c_int32)]
 
 
 class odx_stats(C.Structure):
@@ -154,8 +154,9 @@ def _check(ctx, rc: int, what: str) -> int:
     return rc
 
 
-def odx_set_launch(ctx, block=128, blocks_per_sm=4, chunk=32, persistent=1) -> None:
-    L = odx_launch(block, blocks_per_sm, chunk, persistent)
+def odx_set_launch(ctx, block=128, blocks_per_sm=4, chunk=32, persistent=1,
+                   fp64_batch=16) -> None:
+    L = odx_launch(block, blocks_per_sm, chunk, persistent, fp64_batch)
     _check(ctx, lib().odx_set_launch(ctx, C.byref(L)), "odx_set_launch")
 
 

@@ -57,7 +57,7 @@ __device__ __forceinline__ void geodesic_rhs(const Geo<T> &g, T r, T th, T pr, T
     if constexpr (sizeof(T) == 8) {
         sincos(th, &s, &c);
     } else {
-        __sincosf(th, &s, &c);
+        sincosf(th, &s, &c);
     }
     s = fmax(s, T(kSinFloor));
     const T a = g.a, L = g.L;
@@ -181,61 +181,6 @@ __device__ __forceinline__ double carter_q(double a, double L, const double y[6]
     sincos(y[1], &s, &c);
     s = fmax(s, kSinFloor);
     return y[5] * y[5] + (L * L / (s * s) - a * a) * c * c;
-}
-
-// Analytic torus of the GRRT workload: Keplerian flow Omega = 1/(r^1.5 + a) where r >= r_ISCO
-// and the orbit is timelike at (r, theta), zero-angular-momentum observers elsewhere; thermal
-// emission j = C n_e^2 T^-1/2 exp(-nu0/T), Kirchhoff absorption alpha = j / B_nu(T) with
-// B_nu = 2 nu^3 / (exp(nu/T) - 1); nu0 = nu_obs / g.  Returns the transfer right-hand sides
-// of Eqs. 30-31: dtau/ds = alpha/g, dI/ds = j / (g nu0^3) exp(-tau).
-struct Medium {
-    double ne_index, inv_2w2, T0, T_index, C_norm, r_isco;
-    double freqs[ODX_MAX_FREQ];
-    int n_freq;
-};
-
-template <int NF>
-__device__ __forceinline__ void torus_rhs64(const Medium &m, double a, double L, double r,
-                                            double th, const double *tau, double *ftau,
-                                            double *fI)
-{
-    double s, c;
-    sincos(th, &s, &c);
-    s = fmax(s, kSinFloor);
-    const double r2 = r * r, a2 = a * a, s2 = s * s;
-    const double Sig = r2 + a2 * c * c;
-    const double Del = r2 - 2.0 * r + a2;
-    const double A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
-    const double iS = 1.0 / Sig;
-    const double gtt = -(1.0 - 2.0 * r * iS);
-    const double gtp = -2.0 * a * r * s2 * iS;
-    const double gpp = A * s2 * iS;
-    double Om = 1.0 / (r * sqrt(r) + a);
-    double N = gtt + 2.0 * gtp * Om + gpp * Om * Om;
-    if (!(r >= m.r_isco && N < 0.0)) {
-        Om = 2.0 * a * r / A;
-        N = gtt + 2.0 * gtp * Om + gpp * Om * Om;
-    }
-    const double ig = (1.0 - Om * L) / sqrt(-N);  // 1/g = u^t (1 - Omega L), Eq. 2
-    const double lr = log(r);
-    const double ne = exp(-m.ne_index * lr - c * c * m.inv_2w2);
-    const double iTe = exp(m.T_index * lr) / m.T0;
-    const double pref = m.C_norm * ne * ne * sqrt(iTe);  // C n_e^2 T^-1/2
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        if (k < m.n_freq) {
-            const double nu0 = m.freqs[k] * ig;
-            const double x = nu0 * iTe;
-            const double em = exp(-x);
-            const double om = (x > 0.5) ? 1.0 - em : -expm1(-x);  // 1 - exp(-nu0/T)
-            const double inu3 = 1.0 / (nu0 * nu0 * nu0);
-            ftau[k] = 0.5 * pref * om * inu3 * ig;            // Eq. 30
-            fI[k] = pref * em * inu3 * ig * exp(-tau[k]);     // Eq. 31
-        } else {
-            ftau[k] = 0.0;
-            fI[k] = 0.0;
-        }
-    }
 }
 
 }  // namespace odx

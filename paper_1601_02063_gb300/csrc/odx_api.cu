@@ -25,7 +25,7 @@ using namespace odx;
 struct odx_ctx {
     int device = 0;
     int num_sms = 0;
-    odx_launch launch{128, 4, 32, 1};
+    odx_launch launch{128, 4, 32, 1, 16};
     unsigned long long *queue = nullptr;
     DevStats *stats = nullptr;
     DevScene *scenes = nullptr;
@@ -195,6 +195,7 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     a.stats = ctx->stats;
     a.chunk = ctx->launch.chunk;
     a.persistent = ctx->launch.persistent;
+    a.fp64_batch = ctx->launch.fp64_batch;
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
     cudaError_t e = scenes[0].precision == ODX_MIXED
                         ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st)
@@ -315,6 +316,8 @@ int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *L)
     if (L->chunk < 1 || L->chunk > 4096) return fail(ctx, ODX_ERR_INVALID_ARG, "chunk must be 1..4096");
     if (L->persistent != 0 && L->persistent != 1)
         return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (L->fp64_batch < 1 || L->fp64_batch > 32)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "fp64_batch must be 1..32");
     ctx->launch = *L;
     return ODX_OK;
 }

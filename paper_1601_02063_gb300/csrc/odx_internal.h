@@ -38,6 +38,8 @@ struct TraceArgs {
     DevStats *stats;
     int32_t chunk;
     int32_t persistent;
+    int32_t fp64_batch;
+    int32_t pad;
 };
 
 // Launch the tracing kernel matching (emitter, n_freq, precision) on `stream`.

@@ -19,6 +19,7 @@
 #include "kerr_device.cuh"
 #include "odx_internal.h"
 #include "trace_common.cuh"
+#include "trace_step.cuh"
 
 namespace odx {
 
@@ -35,96 +36,6 @@ struct Ray64 {
     int32_t scene, n_acc, n_rej, n_cross;
 };
 
-template <int NF>
-__device__ __forceinline__ void derivs64(const Geo<double> &g, const Medium &m, const double y[6],
-                                         const double *tau, double f[6], double *ft, double *fI)
-{
-    geodesic_rhs<double>(g, y[0], y[1], y[4], y[5], f);
-    if constexpr (NF > 0) torus_rhs64<NF>(m, g.a, g.L, y[0], y[1], tau, ft, fI);
-}
-
-// One Cash-Karp attempt of size h from (y, tau, I) with first stage (k1, kt1, kI1):
-// fifth-order geodesic y5, embedded error estimate e (geodesic components), and the
-// fifth-order transfer increments dtau, dI.
-template <int NF>
-__device__ __forceinline__ void ck_attempt64(const Geo<double> &g, const Medium &m,
-                                             const double y[6], const double k1[6],
-                                             const double *tau, const double *kt1,
-                                             const double *kI1, double h, double y5[6],
-                                             double e[6], double *dtau, double *dI)
-{
-    constexpr int N = NF + 1;
-    double k2[6], k3[6], k4[6], k5[6], k6[6], yt[6];
-    double t2[N], t3[N], t4[N], t5[N], t6[N], tt[N], fI[N], sI[N];
-#pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] = CK_B1 * kI1[k];
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (CK_A21 * k1[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (CK_A21 * kt1[k]);
-    derivs64<NF>(g, m, yt, tt, k2, t2, fI);
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (CK_A31 * k1[i] + CK_A32 * k2[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (CK_A31 * kt1[k] + CK_A32 * t2[k]);
-    derivs64<NF>(g, m, yt, tt, k3, t3, fI);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += CK_B3 * fI[k];
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        yt[i] = y[i] + h * (CK_A41 * k1[i] + CK_A42 * k2[i] + CK_A43 * k3[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k)
-        tt[k] = tau[k] + h * (CK_A41 * kt1[k] + CK_A42 * t2[k] + CK_A43 * t3[k]);
-    derivs64<NF>(g, m, yt, tt, k4, t4, fI);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += CK_B4 * fI[k];
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        yt[i] = y[i] + h * (CK_A51 * k1[i] + CK_A52 * k2[i] + CK_A53 * k3[i] + CK_A54 * k4[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k)
-        tt[k] = tau[k] + h * (CK_A51 * kt1[k] + CK_A52 * t2[k] + CK_A53 * t3[k] + CK_A54 * t4[k]);
-    derivs64<NF>(g, m, yt, tt, k5, t5, fI);
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-        yt[i] = y[i] + h * (CK_A61 * k1[i] + CK_A62 * k2[i] + CK_A63 * k3[i] + CK_A64 * k4[i] +
-                            CK_A65 * k5[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k)
-        tt[k] = tau[k] + h * (CK_A61 * kt1[k] + CK_A62 * t2[k] + CK_A63 * t3[k] +
-                              CK_A64 * t4[k] + CK_A65 * t5[k]);
-    derivs64<NF>(g, m, yt, tt, k6, t6, fI);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += CK_B6 * fI[k];
-
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        y5[i] = y[i] + h * (CK_B1 * k1[i] + CK_B3 * k3[i] + CK_B4 * k4[i] + CK_B6 * k6[i]);
-        e[i] = h * (CK_E1 * k1[i] + CK_E3 * k3[i] + CK_E4 * k4[i] + CK_E5 * k5[i] +
-                    CK_E6 * k6[i]);
-    }
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        dtau[k] = h * (CK_B1 * kt1[k] + CK_B3 * t3[k] + CK_B4 * t4[k] + CK_B6 * t6[k]);
-        dI[k] = h * sI[k];
-    }
-}
-
-// Geodesic-only Cash-Karp step (fifth-order result), used to localise equatorial crossings.
-__device__ __noinline__ void ck_geo64(const Geo<double> &g, const double y[6], const double k1[6],
-                                      double h, double y5[6])
-{
-    const Medium m{};
-    double e[6], z[1] = {0.0}, d1[1], d2[1];
-    ck_attempt64<0>(g, m, y, k1, z, z, z, h, y5, e, d1, d2);
-}
-
 // Equatorial crossing inside an accepted step: solve cos(theta(sigma)) = 0 for the
 // fifth-order step of size sigma from the step start by Newton's method
 // (d cos(theta)/ds = -sin(theta) dtheta/ds), kept in the sign bracket by bisection, to
@@ -134,13 +45,17 @@ __device__ __noinline__ void locate_crossing64(const Geo<double> &g, const doubl
 {
     double lo = 0.0, hi = h;
     double flo = cos(y[1]);
-    double y5[6];
-    ck_geo64(g, y, k1, h, y5);
+    double y5[6], dy[6];
+    ck_geo_increment<double>(g, y, k1, h, dy);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y5[i] = y[i] + dy[i];
     const double fhi = cos(y5[1]);
     double sig = lo - flo * (hi - lo) / (fhi - flo);
     if (!(sig > lo && sig < hi)) sig = 0.5 * (lo + hi);
     for (int it = 0; it < 60; ++it) {
-        ck_geo64(g, y, k1, sig, y5);
+        ck_geo_increment<double>(g, y, k1, sig, dy);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y5[i] = y[i] + dy[i];
         double sn, F;
         sincos(y5[1], &sn, &F);
         if (fabs(F) <= 1e-14) break;
@@ -198,25 +113,12 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     }
 }
 
-__device__ __forceinline__ void load_medium(const DevScene &S, double a, Medium &m)
-{
-    m.ne_index = S.s.ne_index;
-    m.inv_2w2 = 1.0 / (2.0 * S.s.theta_width * S.s.theta_width);
-    m.T0 = S.s.T0;
-    m.T_index = S.s.T_index;
-    m.C_norm = S.s.C_norm;
-    m.r_isco = isco_radius(a);
-    m.n_freq = S.s.n_freq;
-#pragma unroll
-    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = S.s.freqs[k];
-}
-
 template <int NF>
 __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
 {
     const int lane = threadIdx.x & 31;
     Ray64<NF> R;
-    Medium m{};
+    MediumT<double> m{};
     bool live = false;
     WarpQueue q;
     q.init(A);
@@ -251,9 +153,9 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             R.n_acc = R.n_rej = R.n_cross = 0;
 #pragma unroll
             for (int k = 0; k < NF + 1; ++k) R.tau[k] = R.I[k] = 0.0;
-            if constexpr (NF > 0) load_medium(S, a, m);
+            if constexpr (NF > 0) load_medium_t<double>(S, a, m);
             const Geo<double> g{R.a, R.L, R.sgn};
-            derivs64<NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+            derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
             R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);
             R.hs = R.h;
             live = true;
@@ -269,9 +171,11 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             // ---- one Cash-Karp attempt ----------------------------------------------------------
             const DevScene &S = A.scenes[R.scene];
             const Geo<double> g{R.a, R.L, R.sgn};
-            double y5[6], e[6], dtau[NF + 1], dI[NF + 1];
+            double y5[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
             const double h = R.h;
-            ck_attempt64<NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, y5, e, dtau, dI);
+            ck_attempt<double, NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, dy, e, dtau, dI);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) y5[i] = R.y[i] + dy[i];
             double errmax = 0.0;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -313,7 +217,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                     if (R.y[0] < R.r_stop) {
                         status = ODX_CAPTURED;
                     } else {
-                        derivs64<NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+                        derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
                         if (R.k1[0] > 0.0 && R.y[0] > R.r_start) status = ODX_ESCAPED;
                     }
                     R.h = fmin(h_next, S.s.hmax_frac * R.y[0]);

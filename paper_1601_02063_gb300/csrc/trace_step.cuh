@@ -1,0 +1,234 @@
+// One Cash-Karp step of the geodesic plus radiative transfer, templated on the arithmetic
+// type (double for the FP64 tracer and the FP64 region of the mixed tracer, float for the
+// FP32 bulk of the mixed tracer).  Section 2.1 (Eqs. 4, 5, 9, 12, 14, 15 with the
+// fifth-order adaptive Runge-Kutta scheme) and Section 2.3 (Eqs. 30-31).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kerr_device.cuh"
+
+namespace odx {
+
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+// FP32 emissivity uses the hardware exponential and logarithm (relative error ~1e-6,
+// far below the 1e-3 image tolerance of the reduced-precision path)
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_log(float x) { return __logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ void m_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+
+// Parameters of the analytic torus in the arithmetic type of the step.
+template <typename T>
+struct MediumT {
+    T ne_index, inv_2w2, T0, T_index, C_norm, r_isco;
+    T freqs[ODX_MAX_FREQ];
+    int n_freq;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_medium_t(const DevScene &S, double a, MediumT<T> &m)
+{
+    m.ne_index = (T)S.s.ne_index;
+    m.inv_2w2 = (T)(1.0 / (2.0 * S.s.theta_width * S.s.theta_width));
+    m.T0 = (T)S.s.T0;
+    m.T_index = (T)S.s.T_index;
+    m.C_norm = (T)S.s.C_norm;
+    m.r_isco = (T)isco_radius(a);
+    m.n_freq = S.s.n_freq;
+#pragma unroll
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = (T)S.s.freqs[k];
+}
+
+// Analytic torus (see torus_rhs64 for the model): dtau/ds = alpha/g, dI/ds =
+// j/(g nu0^3) exp(-tau) per observed frequency, nu0 = nu_obs / g.
+template <typename T, int NF>
+__device__ __forceinline__ void torus_rhs(const MediumT<T> &m, T a, T L, T r, T th, const T *tau,
+                                          T *ftau, T *fI)
+{
+    T s, c;
+    m_sincos(th, &s, &c);
+    s = fmax(s, T(kSinFloor));
+    const T r2 = r * r, a2 = a * a, s2 = s * s;
+    const T Sig = r2 + a2 * c * c;
+    const T Del = r2 - T(2) * r + a2;
+    const T A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
+    const T iS = T(1) / Sig;
+    const T gtt = -(T(1) - T(2) * r * iS);
+    const T gtp = -T(2) * a * r * s2 * iS;
+    const T gpp = A * s2 * iS;
+    T Om = T(1) / (r * m_sqrt(r) + a);
+    T N = gtt + T(2) * gtp * Om + gpp * Om * Om;
+    if (!(r >= m.r_isco && N < T(0))) {
+        Om = T(2) * a * r / A;
+        N = gtt + T(2) * gtp * Om + gpp * Om * Om;
+    }
+    const T ig = (T(1) - Om * L) / m_sqrt(-N);  // 1/g = u^t (1 - Omega L), Eq. 2
+    const T lr = m_log(r);
+    const T ne = m_exp(-m.ne_index * lr - c * c * m.inv_2w2);
+    const T iTe = m_exp(m.T_index * lr) / m.T0;
+    const T pref = m.C_norm * ne * ne * m_sqrt(iTe);  // C n_e^2 T^-1/2
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        if (k < m.n_freq) {
+            const T nu0 = m.freqs[k] * ig;
+            const T x = nu0 * iTe;
+            const T em = m_exp(-x);
+            const T om = (x > T(0.5)) ? T(1) - em : -m_expm1(-x);  // 1 - exp(-nu0/T)
+            const T inu3 = T(1) / (nu0 * nu0 * nu0);
+            ftau[k] = T(0.5) * pref * om * inu3 * ig;           // Eq. 30
+            fI[k] = pref * em * inu3 * ig * m_exp(-tau[k]);     // Eq. 31
+        } else {
+            ftau[k] = T(0);
+            fI[k] = T(0);
+        }
+    }
+}
+
+template <typename T, int NF>
+__device__ __forceinline__ void derivs(const Geo<T> &g, const MediumT<T> &m, const T y[6],
+                                       const T *tau, T f[6], T *ft, T *fI)
+{
+    geodesic_rhs<T>(g, y[0], y[1], y[4], y[5], f);
+    if constexpr (NF > 0) torus_rhs<T, NF>(m, g.a, g.L, y[0], y[1], tau, ft, fI);
+}
+
+// Right-hand side evaluated out of line and returned by value: one copy of its code serves
+// all six stages of a step, which keeps the FP32 stage loop inside the instruction cache.
+template <typename T, int NF>
+struct DerivOut {
+    T f[6], ft[NF + 1], fI[NF + 1];
+};
+template <typename T, int NF>
+struct TauIn {
+    T t[NF + 1];
+};
+
+template <typename T, int NF>
+__device__ __noinline__ DerivOut<T, NF> derivs_call(Geo<T> g, MediumT<T> m, T r, T th, T pr, T pth,
+                                                    TauIn<T, NF> tau)
+{
+    DerivOut<T, NF> o;
+    geodesic_rhs<T>(g, r, th, pr, pth, o.f);
+    if constexpr (NF > 0) torus_rhs<T, NF>(m, g.a, g.L, r, th, tau.t, o.ft, o.fI);
+    return o;
+}
+
+// Stage evaluation: inline for FP64 (its pipe, not instruction fetch, bounds it), out of line
+// for FP32.
+template <typename T, int NF>
+__device__ __forceinline__ void derivs_stage(const Geo<T> &g, const MediumT<T> &m, const T y[6],
+                                             const T *tau, T f[6], T *ft, T *fI)
+{
+    if constexpr (sizeof(T) == 4) {
+        TauIn<T, NF> ti;
+#pragma unroll
+        for (int k = 0; k < NF + 1; ++k) ti.t[k] = (k < NF) ? tau[k] : T(0);
+        const DerivOut<T, NF> o = derivs_call<T, NF>(g, m, y[0], y[1], y[4], y[5], ti);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) f[i] = o.f[i];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            ft[k] = o.ft[k];
+            fI[k] = o.fI[k];
+        }
+    } else {
+        derivs<T, NF>(g, m, y, tau, f, ft, fI);
+    }
+}
+
+// One Cash-Karp attempt of size h from (y, tau) with first stage (k1, kt1, kI1).
+// Returns the fifth-order increments dy (y5 = y + dy), the embedded error estimate e of the
+// geodesic components, and the fifth-order increments dtau, dI of the transfer components.
+// tau needs its stage values (dI/ds depends on exp(-tau)); I only its weighted sum.
+template <typename T, int NF>
+__device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m, const T y[6],
+                                           const T k1[6], const T *tau, const T *kt1,
+                                           const T *kI1, T h, T dy[6], T e[6], T *dtau, T *dI)
+{
+    constexpr int N = NF + 1;
+    T k2[6], k3[6], k4[6], k5[6], k6[6], yt[6];
+    T t2[N], t3[N], t4[N], t5[N], t6[N], tt[N], fI[N], sI[N];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] = T(CK_B1) * kI1[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (T(CK_A21) * k1[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (T(CK_A21) * kt1[k]);
+    derivs_stage<T, NF>(g, m, yt, tt, k2, t2, fI);
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (T(CK_A31) * k1[i] + T(CK_A32) * k2[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (T(CK_A31) * kt1[k] + T(CK_A32) * t2[k]);
+    derivs_stage<T, NF>(g, m, yt, tt, k3, t3, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B3) * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (T(CK_A41) * k1[i] + T(CK_A42) * k2[i] + T(CK_A43) * k3[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (T(CK_A41) * kt1[k] + T(CK_A42) * t2[k] + T(CK_A43) * t3[k]);
+    derivs_stage<T, NF>(g, m, yt, tt, k4, t4, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B4) * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (T(CK_A51) * k1[i] + T(CK_A52) * k2[i] + T(CK_A53) * k3[i] +
+                            T(CK_A54) * k4[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (T(CK_A51) * kt1[k] + T(CK_A52) * t2[k] + T(CK_A53) * t3[k] +
+                              T(CK_A54) * t4[k]);
+    derivs_stage<T, NF>(g, m, yt, tt, k5, t5, fI);
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        yt[i] = y[i] + h * (T(CK_A61) * k1[i] + T(CK_A62) * k2[i] + T(CK_A63) * k3[i] +
+                            T(CK_A64) * k4[i] + T(CK_A65) * k5[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)
+        tt[k] = tau[k] + h * (T(CK_A61) * kt1[k] + T(CK_A62) * t2[k] + T(CK_A63) * t3[k] +
+                              T(CK_A64) * t4[k] + T(CK_A65) * t5[k]);
+    derivs_stage<T, NF>(g, m, yt, tt, k6, t6, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B6) * fI[k];
+
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dy[i] = h * (T(CK_B1) * k1[i] + T(CK_B3) * k3[i] + T(CK_B4) * k4[i] + T(CK_B6) * k6[i]);
+        e[i] = h * (T(CK_E1) * k1[i] + T(CK_E3) * k3[i] + T(CK_E4) * k4[i] + T(CK_E5) * k5[i] +
+                    T(CK_E6) * k6[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dtau[k] = h * (T(CK_B1) * kt1[k] + T(CK_B3) * t3[k] + T(CK_B4) * t4[k] + T(CK_B6) * t6[k]);
+        dI[k] = h * sI[k];
+    }
+}
+
+// Geodesic-only fifth-order increment of a single Cash-Karp step of size h from y.
+template <typename T>
+__device__ __noinline__ void ck_geo_increment(const Geo<T> &g, const T y[6], const T k1[6], T h,
+                                              T dy[6])
+{
+    const MediumT<T> m{};
+    T e[6], z[1] = {T(0)}, d1[1], d2[1];
+    ck_attempt<T, 0>(g, m, y, k1, z, z, z, h, dy, e, d1, d2);
+}
+
+}  // namespace odx
