@@ -214,6 +214,31 @@ double odx_torus_norm(double a, double nu, double ne_index, double T0, double T_
 int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops);
 
 /*
+ * A render captured once as a CUDA graph (queue reset + tracing kernel) and replayed: the
+ * batched many-image launch of the parameter sweep, repeated without per-call host work.
+ * The scene table is uploaded at creation into memory the graph owns; every replay renders
+ * the same scenes into the same records_dev / image_dev (layout as odx_render) with the
+ * context's launch shape at creation.  Replays use the context's queue and statistics:
+ * they must not overlap other work on the same context.  Destroy graphs before their
+ * context.
+ */
+typedef struct odx_graph odx_graph;
+int32_t odx_graph_create(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
+                         odx_ray_record *records_dev, double *image_dev, odx_graph **out);
+int32_t odx_graph_launch(odx_graph *graph, void *stream);
+int32_t odx_graph_destroy(odx_graph *graph);
+
+/*
+ * Launch-shape autotuner: renders the given scenes (keep them small: about 10^5 - 10^6 rays)
+ * once per candidate shape (threads per block, resident blocks per SM, queue chunk, FP64
+ * batch, persistent or not), times each with CUDA events on `stream`, sets the fastest on
+ * the context and returns it in *best.  Allocates temporary outputs on the device.
+ * Synchronous.
+ */
+int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
+                     void *stream, odx_launch *best);
+
+/*
  * odx_render without any device allocation, for callers that must not call cudaMalloc:
  * code whose device memory is owned entirely by another allocator (a framework's caching
  * pool, or a fixed budget reserved at start-up) and which must not allocate behind that
@@ -222,7 +247,7 @@ int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops);
  * is a deployment variant of odx_render.
  *
  * The ray queue counter, the device statistics and the scene table live in one file-scope
- * device array of 20,480 bytes that every GPU loading this library holds until the process
+ * device array of 28,672 bytes that every GPU loading this library holds until the process
  * exits; at most ODX_STATIC_MAX_SCENES scenes per call (more: ODX_ERR_TOO_LARGE, nothing
  * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
  * as odx_render) and the scene descriptions in host memory.  The call works on the calling

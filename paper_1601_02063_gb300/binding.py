@@ -94,6 +94,12 @@ _SIGNATURES = [
     ("odx_torus_norm", C.c_double, [C.c_double] * 6),
     ("odx_fma_peak", C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double)]),
     ("odx_render_static", C.c_int32, [C.POINTER(odx_scene), C.c_int32, _P, _P, _P]),
+    ("odx_graph_create", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P, _P,
+                                     C.POINTER(_P)]),
+    ("odx_graph_launch", C.c_int32, [_P, _P]),
+    ("odx_graph_destroy", C.c_int32, [_P]),
+    ("odx_autotune", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P,
+                                 C.POINTER(odx_launch)]),
 ]
 SYMBOLS = [s[0] for s in _SIGNATURES]
 
@@ -154,7 +160,7 @@ def _check(ctx, rc: int, what: str) -> int:
     return rc
 
 
-def odx_set_launch(ctx, block=128, blocks_per_sm=4, chunk=32, persistent=1,
+def odx_set_launch(ctx, block=128, blocks_per_sm=3, chunk=32, persistent=1,
                    fp64_batch=16) -> None:
     L = odx_launch(block, blocks_per_sm, chunk, persistent, fp64_batch)
     _check(ctx, lib().odx_set_launch(ctx, C.byref(L)), "odx_set_launch")
@@ -214,6 +220,30 @@ def odx_render_static(scenes, records_ptr: int, image_ptr: int | None,
     the status code (no context, so no error text)."""
     arr = scene_array(scenes)
     return lib().odx_render_static(arr, len(arr), records_ptr, image_ptr or None, stream or None)
+
+
+def odx_graph_create(ctx, scenes, records_ptr: int, image_ptr: int | None):
+    arr = scene_array(scenes)
+    g = C.c_void_p()
+    _check(ctx, lib().odx_graph_create(ctx, arr, len(arr), records_ptr, image_ptr or None,
+                                       C.byref(g)), "odx_graph_create")
+    return g
+
+
+def odx_graph_launch(ctx, graph, stream: int | None = None) -> None:
+    _check(ctx, lib().odx_graph_launch(graph, stream or None), "odx_graph_launch")
+
+
+def odx_graph_destroy(graph) -> None:
+    lib().odx_graph_destroy(graph)
+
+
+def odx_autotune(ctx, scenes, stream: int | None = None) -> dict:
+    arr = scene_array(scenes)
+    L = odx_launch()
+    _check(ctx, lib().odx_autotune(ctx, arr, len(arr), stream or None, C.byref(L)),
+           "odx_autotune")
+    return {f: getattr(L, f) for f, _ in odx_launch._fields_}
 
 
 # ---- marshalling helpers ----------------------------------------------------------------------

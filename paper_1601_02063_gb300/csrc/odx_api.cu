@@ -25,7 +25,7 @@ using namespace odx;
 struct odx_ctx {
     int device = 0;
     int num_sms = 0;
-    odx_launch launch{128, 4, 32, 1, 16};
+    odx_launch launch{128, 3, 32, 1, 16};
     unsigned long long *queue = nullptr;
     DevStats *stats = nullptr;
     DevScene *scenes = nullptr;
@@ -163,13 +163,10 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
     for (int k = 0; k < n_scenes; ++k) {
         DevScene &d = ctx->host_scenes[k];
-        memset(&d, 0, sizeof(d));
-        d.s = scenes[k];
-        d.ray_begin = ray;
-        d.n_rays = list_mode ? n_list : (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
-        d.img_offset = img;
-        ray += d.n_rays;
-        img += nf * d.n_rays;
+        const int64_t nk = list_mode ? n_list : (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        fill_dev_scene(d, scenes[k], ray, nk, img);
+        ray += nk;
+        img += nf * nk;
     }
     if (total_rays) *total_rays = ray;
     if (total_image) *total_image = img;
@@ -228,9 +225,62 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
     }
 }
 
+// Launch the tracer over a scene table already resident on the device (graph capture).
+int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const odx_scene *scenes,
+                        int32_t n_scenes, int64_t n_total, odx_ray_record *records,
+                        double *image, cudaStream_t st)
+{
+    ODX_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), st));
+    TraceArgs a{};
+    a.scenes = dev_table;
+    a.n_scenes = n_scenes;
+    a.list_mode = 0;
+    a.rays = nullptr;
+    a.n_total = n_total;
+    a.records = records;
+    a.image = image;
+    a.queue = ctx->queue;
+    a.stats = ctx->stats;
+    a.chunk = ctx->launch.chunk;
+    a.persistent = ctx->launch.persistent;
+    a.fp64_batch = ctx->launch.fp64_batch;
+    const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
+    cudaError_t e = scenes[0].precision == ODX_MIXED
+                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st)
+                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "trace kernel launch");
+    return ODX_OK;
+}
+
 }  // namespace
 
+struct odx_graph {
+    odx_ctx *ctx = nullptr;
+    DevScene *table = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace odx {
+void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t n_rays,
+                    int64_t img_offset)
+{
+    memset(&d, 0, sizeof(d));
+    d.s = s;
+    d.ray_begin = ray_begin;
+    d.n_rays = n_rays;
+    d.img_offset = img_offset;
+    d.f_ne_index = (float)s.ne_index;
+    d.f_inv_2w2 = s.theta_width > 0.0 ? (float)(1.0 / (2.0 * s.theta_width * s.theta_width)) : 0.f;
+    d.f_T0 = (float)s.T0;
+    d.f_T_index = (float)s.T_index;
+    d.f_C_norm = (float)s.C_norm;
+    d.f_r_out = (float)s.r_out;
+    d.f_hmax_frac = (float)s.hmax_frac;
+    d.f_rtol32 = (float)s.rtol_fp32;
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) d.f_freqs[k] = (float)s.freqs[k];
+}
+
 // Argument checks of odx_render for callers without a context (no message is stored).
 int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes)
 {
@@ -455,6 +505,137 @@ double odx_torus_norm(double a, double nu, double ne_index, double T0, double T_
         }
     }
     return 1.0 / sum;
+}
+
+int32_t odx_graph_create(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
+                         odx_ray_record *records, double *image, odx_graph **out)
+{
+    if (!ctx || !out) return ODX_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!records || ((uintptr_t)records & 15u) != 0 || (image && ((uintptr_t)image & 7u)))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "records must be 16-byte aligned, image 8-byte");
+    int32_t rc = odx::validate_scene_table(scenes, n_scenes);
+    if (rc != ODX_OK) return fail(ctx, rc, "invalid scene table");
+    rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    std::vector<DevScene> table(n_scenes);
+    const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
+    int64_t ray = 0, img = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        const int64_t nk = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        odx::fill_dev_scene(table[k], scenes[k], ray, nk, img);
+        ray += nk;
+        img += nf * nk;
+    }
+    odx_graph *g = new odx_graph();
+    g->ctx = ctx;
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaMalloc(&g->table, n_scenes * sizeof(DevScene));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->table, table.data(), n_scenes * sizeof(DevScene), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = launch_resident(ctx, g->table, scenes, n_scenes, ray, records, image, cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        g->graph = graph;
+        if (rc == ODX_OK && e2 != cudaSuccess) e = e2;
+        if (rc == ODX_OK && e == cudaSuccess)
+            e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    }
+    if (cap) cudaStreamDestroy(cap);
+    if (e != cudaSuccess || rc != ODX_OK) {
+        odx_graph_destroy(g);
+        return rc != ODX_OK ? rc : cuda_fail(ctx, e, "graph capture");
+    }
+    *out = g;
+    return ODX_OK;
+}
+
+int32_t odx_graph_launch(odx_graph *g, void *stream)
+{
+    if (!g || !g->exec) return ODX_ERR_INVALID_ARG;
+    int32_t rc = set_device(g->ctx);
+    if (rc != ODX_OK) return rc;
+    ODX_CUDA(g->ctx, cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return ODX_OK;
+}
+
+int32_t odx_graph_destroy(odx_graph *g)
+{
+    if (!g) return ODX_OK;
+    cudaSetDevice(g->ctx->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->table) cudaFree(g->table);
+    delete g;
+    return ODX_OK;
+}
+
+int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, void *stream,
+                     odx_launch *best)
+{
+    if (!ctx || !best) return ODX_ERR_INVALID_ARG;
+    int32_t rc = odx::validate_scene_table(scenes, n_scenes);
+    if (rc != ODX_OK) return fail(ctx, rc, "invalid scene table");
+    rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    int64_t nr = 0, ni = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        const int64_t p = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        nr += p;
+        ni += p * (scenes[k].emitter == ODX_EMIT_TORUS ? scenes[k].n_freq : 1);
+    }
+    const bool mixed = scenes[0].precision == ODX_MIXED;
+    std::vector<odx_launch> cands;
+    if (mixed) {
+        for (int bps : {3, 4})
+            for (int chunk : {16, 64})
+                for (int batch : {8, 16, 24}) cands.push_back({128, bps, chunk, 1, batch});
+        cands.push_back({64, 8, 32, 1, 16});
+        cands.push_back({128, 4, 32, 0, 16});
+    } else {
+        for (int block : {64, 128})
+            for (int chunk : {16, 64}) cands.push_back({block, 256 / block * 2, chunk, 1, 16});
+        cands.push_back({128, 4, 32, 0, 16});
+    }
+    void *rec = nullptr, *img = nullptr;
+    ODX_CUDA(ctx, cudaMalloc(&rec, nr * sizeof(odx_ray_record)));
+    cudaError_t e = cudaMalloc(&img, ni * sizeof(double));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const odx_launch saved = ctx->launch;
+    odx_launch winner = saved;
+    float best_ms = 1e30f;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (size_t c = 0; c < cands.size() && e == cudaSuccess && rc == ODX_OK; ++c) {
+        ctx->launch = cands[c];
+        rc = submit(ctx, scenes, n_scenes, nullptr, -1, (odx_ray_record *)rec, (double *)img, st,
+                    nullptr, nullptr);  // warm-up
+        if (rc != ODX_OK) break;
+        e = cudaEventRecord(e0, st);
+        rc = submit(ctx, scenes, n_scenes, nullptr, -1, (odx_ray_record *)rec, (double *)img, st,
+                    nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            winner = cands[c];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rec);
+    if (img) cudaFree(img);
+    ctx->launch = (rc == ODX_OK && e == cudaSuccess) ? winner : saved;
+    if (rc != ODX_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+    *best = winner;
+    return ODX_OK;
 }
 
 int32_t odx_fma_peak(odx_ctx *ctx, int32_t precision, double *flops)

@@ -17,7 +17,14 @@ struct DevScene {
     int64_t n_rays;     // n_alpha * n_beta (list mode: n)
     int64_t img_offset; // offset of this scene's image planes, in doubles
     int64_t pad;
+    // FP32 copies of the parameters the FP32 stages read (filled by fill_dev_scene)
+    float f_ne_index, f_inv_2w2, f_T0, f_T_index, f_C_norm, f_r_out, f_hmax_frac, f_rtol32;
+    float f_freqs[ODX_MAX_FREQ];
 };
+
+// One scene-table entry for a scene whose rays start at ray_begin (all table builders).
+void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t n_rays,
+                    int64_t img_offset);
 
 // Device counters; 64-bit for atomicAdd.
 struct DevStats {

@@ -34,7 +34,7 @@ using odx::DevStats;
 constexpr size_t kQueueOffset = 0;
 constexpr size_t kStatsOffset = 64;
 constexpr size_t kScenesOffset = 256;
-constexpr size_t kStaticBytes = 20480;
+constexpr size_t kStaticBytes = 28672;
 static_assert(kScenesOffset + ODX_STATIC_MAX_SCENES * sizeof(DevScene) <= kStaticBytes,
               "scene table does not fit the static scratch");
 static_assert(sizeof(DevStats) <= kScenesOffset - kStatsOffset, "stats do not fit");
@@ -91,14 +91,10 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
     int64_t ray = 0, img = 0;
     for (int k = 0; k < n_scenes; ++k) {
-        DevScene &d = table[k];
-        memset(&d, 0, sizeof(d));
-        d.s = scenes[k];
-        d.ray_begin = ray;
-        d.n_rays = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
-        d.img_offset = img;
-        ray += d.n_rays;
-        img += nf * d.n_rays;
+        const int64_t nk = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        odx::fill_dev_scene(table[k], scenes[k], ray, nk, img);
+        ray += nk;
+        img += nf * nk;
     }
 
     int dev = 0;
@@ -125,7 +121,7 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     a.image = image;
     a.queue = reinterpret_cast<unsigned long long *>(base + kQueueOffset);
     a.stats = reinterpret_cast<DevStats *>(base + kStatsOffset);
-    const odx_launch launch{128, 4, 32, 1, 16};
+    const odx_launch launch{128, 3, 32, 1, 16};
     a.chunk = launch.chunk;
     a.persistent = launch.persistent;
     a.fp64_batch = launch.fp64_batch;

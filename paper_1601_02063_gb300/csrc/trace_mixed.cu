@@ -1,20 +1,19 @@
 // Mixed-precision backward ray tracer for GB300 (sm_103a).
 //
-// GB300 executes FP32 at 63x the FP64 rate (78.5 vs 1.25 TFLOP/s measured), so the bulk
-// of the Cash-Karp stages runs in FP32 with these FP64 / compensated parts:
-//   - initial state and constants of motion (Section 2.2) in FP64;
-//   - the state y and the transfer integrals tau, I kept as unevaluated float pairs
-//     (hi + lo, ~48-bit) updated with error-free two-sums, so that the accumulation over
-//     hundreds of steps does not add FP32 rounding (compensated sums);
-//   - steps with r < r_switch (near the horizon and the photon orbits) in FP64 with the
-//     FP64 tolerance rtol;
-//   - the null-condition and Carter-constant checks and the disk redshift in FP64.
+// GB300 executes FP32 at 63x the FP64 rate (78.5 vs 1.25 TFLOP/s measured), and an FP64
+// instruction issued by one lane of a warp costs the warp about as much as a full one.  The
+// render is therefore three launches, all per-ray FP64 work done with every lane busy:
+//   1. init pass (FP64, one ray per thread): initial state and constants of motion
+//      (Section 2.2), horizon and ISCO radii, written into the ray's record slot as float
+//      pairs (hi + lo, ~48-bit);
+//   2. tracer (FP32 hot loop, persistent warps): Cash-Karp stages in FP32; the state and
+//      the transfer integrals tau, I kept as float pairs updated with error-free two-sums
+//      (compensated sums); optional FP64 steps where r < r_switch, run per warp once
+//      `fp64_batch` lanes need one; the final state is written back into the record slot;
+//   3. finish pass (FP64, one ray per thread): null-condition and Carter-constant checks,
+//      disk redshift (Eq. 2) and intensity, image in FP64, the final records.
 // Per-ray arithmetic depends only on the ray's own path (the FP32/FP64 choice is made per
 // lane from its own radius), so results do not depend on the launch shape.
-//
-// An FP64 step costs a warp the same whether one lane or 32 take it, so lanes that need
-// one wait until `fp64_batch` lanes of the warp need one (or no FP32 lane is left), and
-// the warp then runs a single FP64 step for all of them.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -24,6 +23,22 @@
 #include "trace_step.cuh"
 
 namespace odx {
+
+// Record slot between the passes (same 80 bytes as odx_ray_record).
+struct MixedInit {  // init pass -> tracer
+    float yh[5], yl[5];  // r, theta, phi, p_r, p_theta (t starts at 0)
+    float Lh, Ll;        // angular momentum
+    float r_stop, r_in, r_isco, a;
+    float h0, r_switch, pad0, pad1;
+};
+struct MixedOut {  // tracer -> finish pass
+    int32_t status, n_acc, n_rej, n_cross;
+    float rch, rcl, pch, pcl;  // first equatorial crossing r, phi (NaN if none)
+    float yh[5], yl[5];        // final r, theta, phi, p_r, p_theta
+    int32_t n64, pad;
+};
+static_assert(sizeof(MixedInit) == sizeof(odx_ray_record), "slot size");
+static_assert(sizeof(MixedOut) == sizeof(odx_ray_record), "slot size");
 
 // (hi, lo) += d, error-free (Knuth two-sum, then renormalisation).
 __device__ __forceinline__ void df_add(float &hi, float &lo, float d)
@@ -45,74 +60,107 @@ __device__ __forceinline__ void df_set(float &hi, float &lo, double v)
 
 __device__ __forceinline__ double df_get(float hi, float lo) { return (double)hi + (double)lo; }
 
+template <typename T>
+__device__ __forceinline__ void store80(void *dst, const T &v)
+{
+    const uint4 *s = reinterpret_cast<const uint4 *>(&v);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) d[i] = s[i];
+}
+
+template <typename T>
+__device__ __forceinline__ T load80(const void *src)
+{
+    T v;
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(&v);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) d[i] = s[i];
+    return v;
+}
+
+__device__ __forceinline__ int state_index(int i) { return i < 3 ? i : i + 1; }  // skip t
+
+// ---- pass 1: FP64 initial state, one ray per thread -------------------------------------
+__global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= A.n_total) return;
+    const DevScene &S = A.scenes[find_scene(A, id)];
+    double alpha, beta, a, theta_obs;
+    ray_inputs(A, S, id, alpha, beta, a, theta_obs);
+    const double sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
+    const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, sgn);
+    MixedInit m;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) df_set(m.yh[i], m.yl[i], io.y[state_index(i)]);
+    df_set(m.Lh, m.Ll, io.L);
+    const double r_isco = isco_radius(a);
+    m.r_stop = (float)(S.s.horizon_factor * horizon_radius(a));
+    m.r_in = (float)((S.s.r_in > 0.0) ? S.s.r_in : r_isco);
+    m.r_isco = (float)r_isco;
+    m.a = (float)a;
+    m.h0 = (float)fmin(S.s.h0, S.s.hmax_frac * io.y[0]);
+    m.r_switch = (float)S.s.r_switch;
+    m.pad0 = m.pad1 = 0.f;
+    store80(A.records + id, m);
+}
+
+// ---- pass 2: FP32 tracer ------------------------------------------------------------------
 template <int NF>
 struct RayM {
-    float yh[6], yl[6];           // state as float pairs: r, theta, phi, t, p_r, p_theta
-    float k1f[6];                 // FP32 first stage (valid when mode == 0)
-    float th[NF + 1], tl[NF + 1]; // tau pairs
-    float Ih[NF + 1], Il[NF + 1]; // invariant intensity pairs
+    float yh[6], yl[6];  // state pairs: r, theta, phi, t, p_r, p_theta
+    float k1f[6];        // FP32 first stage (valid when mode == 0)
+    float th[NF + 1], tl[NF + 1];
+    float Ih[NF + 1], Il[NF + 1];
     float kt1f[NF + 1], kI1f[NF + 1];
-    float hf, hsf;                // FP32 step and error-scale step
-    double hd, hsd;               // FP64 step and error-scale step
-    int32_t mode;                 // 0: FP32 first stage and hf valid, 1: hd valid (FP64)
-    float af, Lf, sgnf, r_switch, hmaxf, r_stopf, r_startf, rtolf;
-    double a, L, Q0;
-    double r_start, r_stop, r_in, r_out;
-    double r_cross, phi_cross;
+    float hf, hsf;       // FP32 step and error-scale step
+    double hd, hsd;      // FP64 step and error-scale step
+    float Lh, Ll, af, sgnf, r_switch, r_stopf, r_startf, r_inf;
+    float rch, rcl, pch, pcl;  // first crossing pairs
     int64_t id;
-    int32_t scene, n_acc, n_rej, n_cross, n64;
+    int32_t scene, mode, n_acc, n_rej, n_cross, n64;
 };
 
 template <int NF>
-__device__ __forceinline__ void state_double(const RayM<NF> &R, double y[6], double *tau)
+__device__ __forceinline__ void write_slot(const TraceArgs &A, const DevScene &S,
+                                           const RayM<NF> &R, int32_t status)
 {
-#pragma unroll
-    for (int i = 0; i < 6; ++i) y[i] = df_get(R.yh[i], R.yl[i]);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) tau[k] = df_get(R.th[k], R.tl[k]);
-}
-
-template <int NF>
-__device__ __forceinline__ void write_result_m(const TraceArgs &A, const DevScene &S,
-                                               const RayM<NF> &R, int32_t status,
-                                               const double yend[6], double r_hit,
-                                               double phi_hit, double g, double inten)
-{
-    RecordOut o;
+    MixedOut o;
     o.status = status;
     o.n_acc = R.n_acc;
     o.n_rej = R.n_rej;
     o.n_cross = R.n_cross;
-    o.r_cross = R.r_cross;
-    o.phi_cross = R.phi_cross;
-    o.r_hit = r_hit;
-    o.phi_hit = phi_hit;
-    o.g = g;
-    o.intensity = inten;
-    o.H_end = null_violation(R.a, R.L, yend);
-    o.Q_drift = (carter_q(R.a, R.L, yend) - R.Q0) / fmax(fabs(R.Q0), 1.0);
-    store_record(A.records + R.id, o);
-    if (A.image) {
-        double *img = A.image + S.img_offset + (R.id - S.ray_begin);
-        if constexpr (NF > 0) {
+    o.rch = R.rch;
+    o.rcl = R.rcl;
+    o.pch = R.pch;
+    o.pcl = R.pcl;
 #pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                if (k < S.s.n_freq) {
-                    const double nu = S.s.freqs[k];
-                    img[(int64_t)k * S.n_rays] = nu * nu * nu * df_get(R.Ih[k], R.Il[k]);
-                }
-            }
-        } else {
-            img[0] = inten;
+    for (int i = 0; i < 5; ++i) {
+        o.yh[i] = R.yh[state_index(i)];
+        o.yl[i] = R.yl[state_index(i)];
+    }
+    o.n64 = R.n64;
+    o.pad = 0;
+    store80(A.records + R.id, o);
+    if constexpr (NF > 0) {
+        if (A.image) {
+            double *img = A.image + S.img_offset + (R.id - S.ray_begin);
+#pragma unroll
+            for (int k = 0; k < NF; ++k)  // packed invariant-intensity pair, finished in pass 3
+                if (k < S.s.n_freq)
+                    *reinterpret_cast<float2 *>(img + (int64_t)k * S.n_rays) =
+                        make_float2(R.Ih[k], R.Il[k]);
         }
     }
 }
 
-// Equatorial crossing in FP32 (same method as the FP64 path, stopping at the FP32
-// resolution of cos(theta)): returns the crossing state as doubles.
+// Equatorial crossing in FP32 (the FP64 method, stopping at the FP32 resolution of
+// cos(theta)); on return the crossing state y + dy is in (ch, cl) as pairs.
 __device__ __noinline__ void locate_crossing32(const Geo<float> &g, const float yh[6],
                                                const float yl[6], const float k1[6], float h,
-                                               double yc[6])
+                                               float ch[6], float cl[6])
 {
     float lo = 0.f, hi = h;
     float flo = cosf(yh[1]);
@@ -144,7 +192,11 @@ __device__ __noinline__ void locate_crossing32(const Geo<float> &g, const float 
         sig = nx;
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) yc[i] = (double)yh[i] + ((double)yl[i] + (double)dy[i]);
+    for (int i = 0; i < 6; ++i) {
+        ch[i] = yh[i];
+        cl[i] = yl[i];
+        df_add(ch[i], cl[i], dy[i]);
+    }
 }
 
 __device__ __noinline__ void locate_crossing64m(const Geo<double> &g, const double y[6],
@@ -182,28 +234,54 @@ __device__ __noinline__ void locate_crossing64m(const Geo<double> &g, const doub
     for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
 }
 
-// Disk hit with the crossing state yc (FP64): returns true when the ray stops on the disk.
-template <int NF>
-__device__ __forceinline__ bool disk_hit(const TraceArgs &A, const DevScene &S,
-                                         const RayM<NF> &R, const double yc[6])
+__device__ __forceinline__ MediumT<float> medium32(const DevScene &S, float r_isco)
 {
-    if (S.s.emitter != ODX_EMIT_THIN_DISK || !(yc[0] >= R.r_in && yc[0] <= R.r_out)) return false;
-    const double gz = disk_redshift(R.a, yc[0], R.L);
-    const double g2 = gz * gz;
-    const double inten = g2 * g2 * pow(yc[0], -S.s.q_emis);
-    write_result_m<NF>(A, S, R, ODX_DISK_HIT, yc, yc[0], yc[2], gz, inten);
-    return true;
+    MediumT<float> m;
+    m.ne_index = S.f_ne_index;
+    m.inv_2w2 = S.f_inv_2w2;
+    m.T0 = S.f_T0;
+    m.T_index = S.f_T_index;
+    m.C_norm = S.f_C_norm;
+    m.r_isco = r_isco;
+    m.n_freq = S.s.n_freq;
+#pragma unroll
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = S.f_freqs[k];
+    return m;
+}
+
+// Record the crossing; returns true when the ray stops on the thin disk (the crossing state
+// becomes the final state).
+template <int NF>
+__device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, const float ch[6],
+                                            const float cl[6])
+{
+    ++R.n_cross;
+    if (R.n_cross == 1) {
+        R.rch = ch[0];
+        R.rcl = cl[0];
+        R.pch = ch[2];
+        R.pcl = cl[2];
+    }
+    if (S.s.emitter == ODX_EMIT_THIN_DISK && ch[0] >= R.r_inf && ch[0] <= S.f_r_out) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            R.yh[i] = ch[i];
+            R.yl[i] = cl[i];
+        }
+        return true;
+    }
+    return false;
 }
 
 // One FP32 Cash-Karp attempt.  Returns the new status.
 template <int NF>
-__device__ __forceinline__ int32_t step32(const TraceArgs &A, const DevScene &S, RayM<NF> &R,
+__device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R,
                                           const MediumT<float> &mf)
 {
-    const Geo<float> g{R.af, R.Lf, R.sgnf};
+    const Geo<float> g{R.af, R.Lh, R.sgnf};
     if (R.mode != 0) {  // (re)enter FP32: first stage in FP32
         derivs_stage<float, NF>(g, mf, R.yh, R.th, R.k1f, R.kt1f, R.kI1f);
-        R.hf = (float)R.hd;
+        if (R.mode == 1) R.hf = (float)R.hd;
         R.hsf = R.hf;
         R.mode = 0;
     }
@@ -216,24 +294,19 @@ __device__ __forceinline__ int32_t step32(const TraceArgs &A, const DevScene &S,
         const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * R.k1f[i]) + 1e-30f;
         errmax = fmaxf(errmax, fabsf(e[i] / sc));
     }
-    errmax /= R.rtolf;
+    errmax /= S.f_rtol32;
     if (isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.f)) {
         ++R.n_rej;
-        R.hf = fmaxf(0.9f * h * powf(errmax, -0.25f), 0.1f * h);
+        R.hf = fmaxf(0.9f * h * __powf(errmax, -0.25f), 0.1f * h);
         return R.hf < 1e-12f ? ODX_NUMERR : ODX_RUNNING;
     }
     ++R.n_acc;
-    const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * powf(errmax, -0.2f) : 5.f * h;
+    const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
     if ((cosf(R.yh[1]) > 0.f) != (cosf(R.yh[1] + dy[1]) > 0.f)) {
-        double yc[6];
-        locate_crossing32(g, R.yh, R.yl, R.k1f, h, yc);
-        ++R.n_cross;
-        if (R.n_cross == 1) {
-            R.r_cross = yc[0];
-            R.phi_cross = yc[2];
-        }
-        if (disk_hit<NF>(A, S, R, yc)) return ODX_DISK_HIT;
+        float ch[6], cl[6];
+        locate_crossing32(g, R.yh, R.yl, R.k1f, h, ch, cl);
+        if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) df_add(R.yh[i], R.yl[i], dy[i]);
@@ -245,22 +318,38 @@ __device__ __forceinline__ int32_t step32(const TraceArgs &A, const DevScene &S,
     if (R.yh[0] < R.r_stopf) return ODX_CAPTURED;
     derivs_stage<float, NF>(g, mf, R.yh, R.th, R.k1f, R.kt1f, R.kI1f);
     if (R.k1f[0] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
-    R.hf = fminf(h_next, R.hmaxf * R.yh[0]);
+    R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
     R.hsf = R.hf;
     return ODX_RUNNING;
 }
 
 // One FP64 Cash-Karp attempt on the pair state (FP64 tolerance rtol).  The first stage is
-// evaluated afresh in FP64 (FP64 steps are rare and batched; keeping an FP64 first stage
-// alive across the FP32 steps would cost 2 x (6 + 2 NF) registers on every step).
+// evaluated afresh in FP64: FP64 steps are rare and batched, and keeping an FP64 first stage
+// alive across the FP32 steps would cost 2 x (6 + 2 NF) registers on every step.
 template <int NF>
-__device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, RayM<NF> &R)
+__device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, RayM<NF> &R,
+                                       float r_isco)
 {
-    const Geo<double> g{R.a, R.L, (double)R.sgnf};
+    const double a = A.list_mode ? A.rays[4 * R.id + 2] : S.s.a;
+    const double L = df_get(R.Lh, R.Ll);
+    const Geo<double> g{a, L, (double)R.sgnf};
     MediumT<double> md{};
-    if constexpr (NF > 0) load_medium_t<double>(S, R.a, md);
+    if constexpr (NF > 0) {
+        md.ne_index = S.s.ne_index;
+        md.inv_2w2 = 1.0 / (2.0 * S.s.theta_width * S.s.theta_width);
+        md.T0 = S.s.T0;
+        md.T_index = S.s.T_index;
+        md.C_norm = S.s.C_norm;
+        md.r_isco = (double)r_isco;
+        md.n_freq = S.s.n_freq;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) md.freqs[k] = S.s.freqs[k];
+    }
     double y[6], tau[NF + 1], k1[6], kt1[NF + 1], kI1[NF + 1];
-    state_double<NF>(R, y, tau);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = df_get(R.yh[i], R.yl[i]);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) tau[k] = df_get(R.th[k], R.tl[k]);
     derivs<double, NF>(g, md, y, tau, k1, kt1, kI1);
     if (R.mode != 1) {  // entering FP64
         R.hd = (double)R.hf;
@@ -289,12 +378,10 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     if ((cos(y[1]) > 0.0) != (cos(y[1] + dy[1]) > 0.0)) {
         double yc[6];
         locate_crossing64m(g, y, k1, h, yc);
-        ++R.n_cross;
-        if (R.n_cross == 1) {
-            R.r_cross = yc[0];
-            R.phi_cross = yc[2];
-        }
-        if (disk_hit<NF>(A, S, R, yc)) return ODX_DISK_HIT;
+        float ch[6], cl[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) df_set(ch[i], cl[i], yc[i]);
+        if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -307,9 +394,9 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
         df_set(R.th[k], R.tl[k], tau[k]);
         df_set(R.Ih[k], R.Il[k], df_get(R.Ih[k], R.Il[k]) + dI[k]);
     }
-    if (y[0] < R.r_stop) return ODX_CAPTURED;
-    // escape test: dr/ds at the new point (sgn * Delta p_r / Sigma has the sign of sgn * p_r)
-    if (R.sgnf * (float)y[4] > 0.f && y[0] > R.r_start) return ODX_ESCAPED;
+    if (R.yh[0] < R.r_stopf) return ODX_CAPTURED;
+    // escape test: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
+    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
     R.hd = fmin(h_next, S.s.hmax_frac * y[0]);
     R.hsd = R.hd;
     R.hf = (float)R.hd;
@@ -332,43 +419,34 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
     for (;;) {
         int64_t id;
         q.refill(A, lane, live, id);
-        if (id >= 0) {
+        if (id >= 0) {  // refill from the init pass's slot: no FP64 work here
             const int32_t sidx = find_scene(A, id);
             const DevScene &S = A.scenes[sidx];
-            double alpha, beta, a, theta_obs;
-            ray_inputs(A, S, id, alpha, beta, a, theta_obs);
-            const double sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
-            const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, sgn);
+            const MixedInit m = load80<MixedInit>(A.records + id);
             R.id = id;
             R.scene = sidx;
-            R.a = a;
-            R.L = io.L;
-            R.Q0 = io.Q;
-            R.af = (float)a;
-            R.Lf = (float)io.L;
-            R.sgnf = (float)sgn;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) df_set(R.yh[i], R.yl[i], io.y[i]);
+            for (int i = 0; i < 5; ++i) {
+                R.yh[state_index(i)] = m.yh[i];
+                R.yl[state_index(i)] = m.yl[i];
+            }
+            R.yh[3] = R.yl[3] = 0.f;
+            R.Lh = m.Lh;
+            R.Ll = m.Ll;
+            R.af = m.a;
+            R.sgnf = (S.s.convention == ODX_CONV_LITERAL) ? 1.f : -1.f;
+            R.r_switch = m.r_switch;
+            R.r_stopf = m.r_stop;
+            R.r_inf = m.r_in;
+            R.r_startf = m.yh[0];
 #pragma unroll
             for (int k = 0; k < NF + 1; ++k) R.th[k] = R.tl[k] = R.Ih[k] = R.Il[k] = 0.f;
-            R.r_start = io.y[0];
-            R.r_stop = S.s.horizon_factor * horizon_radius(a);
-            R.r_in = (S.s.r_in > 0.0) ? S.s.r_in : isco_radius(a);
-            R.r_out = S.s.r_out;
-            R.r_startf = (float)R.r_start;
-            R.r_stopf = (float)R.r_stop;
-            R.r_switch = (float)S.s.r_switch;
-            R.hmaxf = (float)S.s.hmax_frac;
-            R.rtolf = (float)S.s.rtol_fp32;
-            R.r_cross = qnan();
-            R.phi_cross = qnan();
+            R.rch = R.rcl = R.pch = R.pcl = __int_as_float(0x7fc00000);
             R.n_acc = R.n_rej = R.n_cross = R.n64 = 0;
-            R.hd = fmin(S.s.h0, S.s.hmax_frac * io.y[0]);
-            R.hsd = R.hd;
-            R.hf = (float)R.hd;
-            R.hsf = R.hf;
+            R.hf = m.h0;
+            R.hsf = m.h0;
             R.mode = -1;
-            if constexpr (NF > 0) load_medium_t<float>(S, a, mf);
+            if constexpr (NF > 0) mf = medium32(S, m.r_isco);
             live = true;
         }
         const unsigned act = __ballot_sync(kFull, live);
@@ -390,19 +468,14 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
                 // the FP64 step works on a copy: only this rare path pays for moving the ray
                 // state through local memory, and the FP32 path keeps its registers
                 RayM<NF> t = R;
-                status = step64<NF>(A, S, t);
+                status = step64<NF>(A, S, t, mf.r_isco);
                 R = t;
             } else {
-                status = step32<NF>(A, S, R, mf);
+                status = step32<NF>(S, R, mf);
             }
             if (status == ODX_RUNNING && R.n_acc + R.n_rej >= S.s.max_steps) status = ODX_MAXSTEPS;
             if (status != ODX_RUNNING) {
-                if (status != ODX_DISK_HIT) {
-                    double yend[6];
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) yend[i] = df_get(R.yh[i], R.yl[i]);
-                    write_result_m<NF>(A, S, R, status, yend, qnan(), qnan(), qnan(), 0.0);
-                }
+                write_slot<NF>(A, S, R, status);
                 my_rays += 1;
                 my_acc += R.n_acc;
                 my_rej += R.n_rej;
@@ -412,6 +485,54 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
         }
     }
     flush_stats(A, lane, my_rays, my_acc, my_rej, my_64, my_slots, my_active);
+}
+
+// ---- pass 3: FP64 checks, redshift, intensity, final records -----------------------------
+__global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= A.n_total) return;
+    const DevScene &S = A.scenes[find_scene(A, id)];
+    const MixedOut o = load80<MixedOut>(A.records + id);
+    double alpha, beta, a, theta_obs;
+    ray_inputs(A, S, id, alpha, beta, a, theta_obs);
+    const double sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
+    const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, sgn);
+    double yend[6];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) yend[state_index(i)] = df_get(o.yh[i], o.yl[i]);
+    yend[3] = 0.0;
+    RecordOut r;
+    r.status = o.status;
+    r.n_acc = o.n_acc;
+    r.n_rej = o.n_rej;
+    r.n_cross = o.n_cross;
+    r.r_cross = df_get(o.rch, o.rcl);
+    r.phi_cross = df_get(o.pch, o.pcl);
+    r.H_end = null_violation(a, io.L, yend);
+    r.Q_drift = (carter_q(a, io.L, yend) - io.Q) / fmax(fabs(io.Q), 1.0);
+    r.r_hit = r.phi_hit = r.g = qnan();
+    r.intensity = 0.0;
+    if (o.status == ODX_DISK_HIT) {
+        r.r_hit = yend[0];
+        r.phi_hit = yend[2];
+        r.g = disk_redshift(a, yend[0], io.L);
+        const double g2 = r.g * r.g;
+        r.intensity = g2 * g2 * pow(yend[0], -S.s.q_emis);
+    }
+    store_record(A.records + id, r);
+    if (A.image) {
+        double *img = A.image + S.img_offset + (id - S.ray_begin);
+        if (S.s.emitter == ODX_EMIT_TORUS) {
+            for (int k = 0; k < S.s.n_freq; ++k) {
+                const float2 p = *reinterpret_cast<const float2 *>(img + (int64_t)k * S.n_rays);
+                const double nu = S.s.freqs[k];
+                img[(int64_t)k * S.n_rays] = nu * nu * nu * df_get(p.x, p.y);
+            }
+        } else {
+            img[0] = r.intensity;
+        }
+    }
 }
 
 template <int NF>
@@ -430,13 +551,21 @@ cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const od
                                int32_t num_sms, cudaStream_t st)
 {
     if (L.block > 128) return cudaErrorInvalidValue;
+    if (args.n_total <= 0) return cudaSuccess;
+    const unsigned pass_blocks = (unsigned)((args.n_total + 127) / 128);
+    mixed_init_kernel<<<pass_blocks, 128, 0, st>>>(args);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const dim3 grid = trace_grid(args, L, num_sms);
     switch (nf_slots) {
-    case 0: return launch_mixed_nf<0>(args, L, grid, st);
-    case 4: return launch_mixed_nf<4>(args, L, grid, st);
-    case 8: return launch_mixed_nf<8>(args, L, grid, st);
+    case 0: e = launch_mixed_nf<0>(args, L, grid, st); break;
+    case 4: e = launch_mixed_nf<4>(args, L, grid, st); break;
+    case 8: e = launch_mixed_nf<8>(args, L, grid, st); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
+    mixed_finish_kernel<<<pass_blocks, 128, 0, st>>>(args);
+    return cudaGetLastError();
 }
 
 }  // namespace odx
