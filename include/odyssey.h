@@ -239,6 +239,60 @@ int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scene
                      void *stream, odx_launch *best);
 
 /*
+ * Learned thin-disk transfer function (the surrogate): an MLP
+ * (alpha/20, beta/20, a, cos i) -> (capture logit, ln r, phi / pi, g) with 4 hidden layers
+ * of 256 SiLU units, BF16 weights and activations, FP32 accumulation, trained on rays the
+ * integrator traces.  (r, phi) is the disk hit for rays that stop on the thin disk, else
+ * the first equatorial crossing; g the disk redshift (Eq. 2) at the hit.
+ * Parameters (FP32 master copy, flat, ODX_MLP_PARAMS floats): W1[4][256], b1[256], then for
+ * each of the three 256 x 256 layers W[256][256] (row = input unit), b[256], then
+ * W5[256][4], b5[4].  Weights enter the kernels rounded to BF16; biases are added in FP32.
+ * Loss over a batch of n rows with targets t[n][8] = (captured, ln r, phi / pi, g,
+ * mask_cross, mask_g, 0, 0):  mean over rows of
+ *   BCE(logit, captured) + mask_cross ((y1 - t1)^2 + (y2 - t2)^2) + mask_g (y3 - t3)^2.
+ * Training uses Adam (beta1 0.9, beta2 0.999, eps 1e-8).  The paper has no learned
+ * component; this is the surrogate of the thin-disk images of Section 4.3.
+ */
+#define ODX_MLP_IN 4
+#define ODX_MLP_HIDDEN 256
+#define ODX_MLP_DEPTH 4
+#define ODX_MLP_OUT 4
+#define ODX_MLP_PARAMS 199684
+typedef struct odx_mlp odx_mlp;
+/* max_batch: rows per training step / inference chunk (rounded up to 128, <= 2^22). */
+int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp **out);
+int32_t odx_mlp_destroy(odx_mlp *mlp);
+int32_t odx_mlp_get_params(odx_mlp *mlp, float *params_host);
+int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Adam state */
+/* y_dev[n][4] = MLP(x_dev[n][4]), any n (processed in chunks of max_batch). */
+int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
+/* Loss and gradients (dL/dparams, layout as the parameters) of one batch, n a multiple of
+ * 128 and <= max_batch; synchronous, results copied to host (either may be NULL). */
+int32_t odx_mlp_gradients(odx_mlp *mlp, const float *x_dev, const float *t_dev, int64_t n,
+                          float *grad_host, float *loss_host);
+/* One Adam step on a batch (n a multiple of 128, <= max_batch); loss_dev: 1 float or NULL. */
+int32_t odx_mlp_train_step(odx_mlp *mlp, const float *x_dev, const float *t_dev, int64_t n,
+                           float lr, float *loss_dev, void *stream);
+/* Inputs and targets from traced rays (odx_trace_rays with a thin-disk prototype):
+ * x_dev[n_pad][4], t_dev[n_pad][8] with n_pad = n rounded up to 128 (padding rows zero);
+ * crossings beyond r_max are masked. */
+int32_t odx_mlp_targets(odx_ctx *ctx, const odx_ray_record *records_dev, const double *rays_dev,
+                        int64_t n, double r_max, float *x_dev, float *t_dev, void *stream);
+/*
+ * Surrogate render of a thin-disk scene into image_dev[n_beta][n_alpha]: the MLP classifies
+ * every pixel; pixels within `band` (M) of the Bardeen critical curve along their polar
+ * angle, or with capture probability in [p_lo, p_hi], fall back to the ray tracer (the
+ * scene's precision), whose records go to fallback_records_dev (capacity n_alpha*n_beta),
+ * their flat pixel indices to fallback_pixels_dev (same capacity; may be NULL), and whose
+ * intensities replace the surrogate's.  *n_fallback = number of fallback rays.
+ * Synchronous (the fallback count is read back to size the tracer launch).
+ */
+int32_t odx_surrogate_render(odx_mlp *mlp, const odx_scene *scene_host, double band, double p_lo,
+                             double p_hi, odx_ray_record *fallback_records_dev,
+                             int64_t *fallback_pixels_dev, double *image_dev,
+                             int64_t *n_fallback, void *stream);
+
+/*
  * odx_render without any device allocation, for callers that must not call cudaMalloc:
  * code whose device memory is owned entirely by another allocator (a framework's caching
  * pool, or a fixed budget reserved at start-up) and which must not allocate behind that

@@ -100,7 +100,18 @@ _SIGNATURES = [
     ("odx_graph_destroy", C.c_int32, [_P]),
     ("odx_autotune", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P,
                                  C.POINTER(odx_launch)]),
+    ("odx_mlp_create", C.c_int32, [_P, C.c_int64, C.c_uint64, C.POINTER(_P)]),
+    ("odx_mlp_destroy", C.c_int32, [_P]),
+    ("odx_mlp_get_params", C.c_int32, [_P, _P]),
+    ("odx_mlp_set_params", C.c_int32, [_P, _P]),
+    ("odx_mlp_forward", C.c_int32, [_P, _P, C.c_int64, _P, _P]),
+    ("odx_mlp_gradients", C.c_int32, [_P, _P, _P, C.c_int64, _P, _P]),
+    ("odx_mlp_train_step", C.c_int32, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
+    ("odx_mlp_targets", C.c_int32, [_P, _P, _P, C.c_int64, C.c_double, _P, _P, _P]),
+    ("odx_surrogate_render", C.c_int32, [_P, C.POINTER(odx_scene), C.c_double, C.c_double,
+                                         C.c_double, _P, _P, _P, C.POINTER(C.c_int64), _P]),
 ]
+MLP_PARAMS = 199684
 SYMBOLS = [s[0] for s in _SIGNATURES]
 
 _lib = None
@@ -244,6 +255,67 @@ def odx_autotune(ctx, scenes, stream: int | None = None) -> dict:
     _check(ctx, lib().odx_autotune(ctx, arr, len(arr), stream or None, C.byref(L)),
            "odx_autotune")
     return {f: getattr(L, f) for f, _ in odx_launch._fields_}
+
+
+def _ok(rc: int, what: str) -> None:
+    if rc != OK:
+        raise OdxError(rc, what)
+
+
+def odx_mlp_create(ctx, max_batch: int, seed: int):
+    h = C.c_void_p()
+    _ok(lib().odx_mlp_create(ctx, max_batch, seed, C.byref(h)), "odx_mlp_create")
+    return h
+
+
+def odx_mlp_destroy(mlp) -> None:
+    lib().odx_mlp_destroy(mlp)
+
+
+def odx_mlp_get_params(mlp) -> np.ndarray:
+    out = np.empty(MLP_PARAMS, dtype=np.float32)
+    _ok(lib().odx_mlp_get_params(mlp, out.ctypes.data), "odx_mlp_get_params")
+    return out
+
+
+def odx_mlp_set_params(mlp, params: np.ndarray) -> None:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == MLP_PARAMS
+    _ok(lib().odx_mlp_set_params(mlp, p.ctypes.data), "odx_mlp_set_params")
+
+
+def odx_mlp_forward(mlp, x_ptr: int, n: int, y_ptr: int, stream: int | None = None) -> None:
+    _ok(lib().odx_mlp_forward(mlp, x_ptr, n, y_ptr, stream or None), "odx_mlp_forward")
+
+
+def odx_mlp_gradients(mlp, x_ptr: int, t_ptr: int, n: int):
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _ok(lib().odx_mlp_gradients(mlp, x_ptr, t_ptr, n, g.ctypes.data, loss.ctypes.data),
+        "odx_mlp_gradients")
+    return g, float(loss[0])
+
+
+def odx_mlp_train_step(mlp, x_ptr: int, t_ptr: int, n: int, lr: float, loss_ptr: int | None,
+                       stream: int | None = None) -> None:
+    _ok(lib().odx_mlp_train_step(mlp, x_ptr, t_ptr, n, lr, loss_ptr or None, stream or None),
+        "odx_mlp_train_step")
+
+
+def odx_mlp_targets(ctx, rec_ptr: int, rays_ptr: int, n: int, r_max: float, x_ptr: int,
+                    t_ptr: int, stream: int | None = None) -> None:
+    _check(ctx, lib().odx_mlp_targets(ctx, rec_ptr, rays_ptr, n, r_max, x_ptr, t_ptr,
+                                      stream or None), "odx_mlp_targets")
+
+
+def odx_surrogate_render(mlp, scene, band: float, p_lo: float, p_hi: float, fb_rec_ptr: int,
+                         fb_pix_ptr: int | None, image_ptr: int, stream: int | None = None) -> int:
+    arr = scene_array([scene])
+    n_fb = C.c_int64()
+    _ok(lib().odx_surrogate_render(mlp, arr, band, p_lo, p_hi, fb_rec_ptr, fb_pix_ptr or None,
+                                   image_ptr, C.byref(n_fb), stream or None),
+        "odx_surrogate_render")
+    return n_fb.value
 
 
 # ---- marshalling helpers ----------------------------------------------------------------------

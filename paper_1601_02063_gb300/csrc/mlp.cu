@@ -1,0 +1,717 @@
+// Learned thin-disk transfer function (alpha, beta, a, cos i) -> (capture logit, log r_cross,
+// phi_cross / pi, g): 4 -> 256 -> 256 -> 256 -> 256 -> 4 with SiLU, BF16 weights and
+// activations, FP32 accumulation.  Training (forward, backward, Adam) and inference run in
+// the kernels below; the 256 x 256 layers use the BF16 tensor-core GEMM of mlp_gemm.cuh,
+// the 4-wide input and output layers are CUDA-core kernels.  The surrogate render
+// classifies each pixel and hands the uncertain ones (near the Bardeen critical curve or
+// with an unsure capture probability) back to the ray tracer.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kerr_device.cuh"
+#include "mlp_gemm.cuh"
+#include "odx_internal.h"
+
+namespace odx {
+cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                               int32_t num_sms, cudaStream_t st);
+cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                              int32_t num_sms, cudaStream_t st);
+int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes);
+void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t n_rays,
+                    int64_t img_offset);
+struct CtxView {
+    int device, num_sms;
+    odx_launch launch;
+    unsigned long long *queue;
+    DevStats *stats;
+};
+int32_t ctx_view(odx_ctx *ctx, CtxView *v);
+}  // namespace odx
+
+using namespace odx;
+using namespace odx::mlp;
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+constexpr int HID = ODX_MLP_HIDDEN, NIN = 4, NOUT = 4, NLAYER_HIDDEN = ODX_MLP_DEPTH;
+// flat FP32 parameter layout: W1[4][256] b1[256] (W[256][256] b[256]) x 3 W5[256][4] b5[4]
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NIN * HID;
+constexpr int OFF_W2 = OFF_B1 + HID;
+constexpr int LAYER_SZ = HID * HID + HID;
+constexpr int OFF_W5 = OFF_W2 + (NLAYER_HIDDEN - 1) * LAYER_SZ;
+constexpr int OFF_B5 = OFF_W5 + HID * NOUT;
+constexpr int NPARAM = OFF_B5 + NOUT;
+static_assert(NPARAM == ODX_MLP_PARAMS, "parameter count");
+
+__host__ __device__ constexpr int off_w(int l) { return OFF_W2 + (l - 2) * LAYER_SZ; }  // l = 2..4
+__host__ __device__ constexpr int off_b(int l) { return off_w(l) + HID * HID; }
+
+}  // namespace
+
+struct odx_mlp {
+    odx_ctx *ctx = nullptr;
+    int device = 0;
+    int64_t max_batch = 0;  // multiple of 128
+    float *p = nullptr;      // FP32 master parameters
+    bf16 *pb = nullptr;      // BF16 copy used by the kernels
+    float *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    int64_t step = 0;
+    bf16 *Z[5] = {}, *H[5] = {};  // layers 1..4
+    bf16 *dZ = nullptr, *dZ2 = nullptr;
+    float *Y = nullptr, *dY = nullptr, *loss = nullptr;
+    float *xin = nullptr;   // padded input rows for inference
+    // surrogate render workspace
+    int64_t surr_cap = 0;
+    float *surr_x = nullptr, *surr_y = nullptr;
+    double *fb_rays = nullptr;
+    int64_t *fb_pix = nullptr;
+    unsigned long long *fb_count = nullptr;
+    float *bcrit = nullptr;  // critical-curve table
+    DevScene *scene_tab = nullptr;
+};
+
+namespace {
+
+#define MLP_CUDA(call)                                   \
+    do {                                                 \
+        if ((call) != cudaSuccess) return ODX_ERR_CUDA;  \
+    } while (0)
+
+__device__ __forceinline__ float bfv(const bf16 *p, int64_t i) { return __bfloat162float(p[i]); }
+
+// ---- layer 1 (4 -> 256) and layer 5 (256 -> 4) on CUDA cores ------------------------------
+// weights from the BF16 copy, biases from the FP32 master (added in the FP32 epilogue)
+__global__ void layer1_fwd(const float *__restrict__ x, const bf16 *__restrict__ pb,
+                           const float *__restrict__ p, int64_t B, bf16 *Z, bf16 *H)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * HID) return;
+    const int64_t b = idx / HID;
+    const int n = (int)(idx % HID);
+    float z = p[OFF_B1 + n];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) z += x[b * NIN + k] * bfv(pb, OFF_W1 + k * HID + n);
+    if (Z) Z[idx] = __float2bfloat16_rn(z);
+    H[idx] = __float2bfloat16_rn(silu(z));
+}
+
+// One warp per sample row: y = H4 . W5 + b5 (lane-strided dot products, warp reduction);
+// with targets: loss and dL/dy (1/B folded in).
+__global__ void layer5_fwd_loss(const bf16 *__restrict__ H4, const bf16 *__restrict__ pb,
+                                const float *__restrict__ p, int64_t B, int64_t B_true, float *Y,
+                                const float *__restrict__ t, float *dY, float *loss)
+{
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float y[NOUT] = {0.f, 0.f, 0.f, 0.f};
+    for (int n = lane; n < HID; n += 32) {
+        const float h = bfv(H4, b * HID + n);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) y[o] += h * bfv(pb, OFF_W5 + n * NOUT + o);
+    }
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) y[o] += __shfl_xor_sync(0xffffffffu, y[o], s);
+        y[o] += p[OFF_B5 + o];
+    }
+    if (lane == 0) {
+        if (Y) {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) Y[b * NOUT + o] = y[o];
+        }
+        if (t) {
+            const float *tb = t + b * 8;
+            const float c = tb[0], mx = tb[4], mg = tb[5];
+            const float inv = (b < B_true) ? 1.f / (float)B_true : 0.f;
+            const float sp = fmaxf(y[0], 0.f) - c * y[0] + log1pf(__expf(-fabsf(y[0])));
+            const float e1 = y[1] - tb[1], e2 = y[2] - tb[2], e3 = y[3] - tb[3];
+            const float l = sp + mx * (e1 * e1 + e2 * e2) + mg * e3 * e3;
+            dY[b * NOUT + 0] = inv * (1.f / (1.f + __expf(-y[0])) - c);
+            dY[b * NOUT + 1] = inv * 2.f * mx * e1;
+            dY[b * NOUT + 2] = inv * 2.f * mx * e2;
+            dY[b * NOUT + 3] = inv * 2.f * mg * e3;
+            if (b < B_true) atomicAdd(loss, l * inv);
+        }
+    }
+}
+
+// dZ4 = (dY W5^T) * silu'(Z4), one thread per (b, n).
+__global__ void layer5_bwd_dz(const float *__restrict__ dY, const bf16 *__restrict__ pb,
+                              const bf16 *__restrict__ Z4, int64_t B, bf16 *dZ4)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * HID) return;
+    const int64_t b = idx / HID;
+    const int n = (int)(idx % HID);
+    float v = 0.f;
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) v += dY[b * NOUT + o] * bfv(pb, OFF_W5 + n * NOUT + o);
+    dZ4[idx] = __float2bfloat16_rn(v * dsilu(__bfloat162float(Z4[idx])));
+}
+
+// Column reductions over a chunk of 256 rows per block, thread n:
+//   g_out[n][o] += sum_b Hin[b][n] * dY[b][o]  (dW5) and g_b[o] += sum_b dY[b][o] (db5)
+__global__ void layer5_bwd_w(const bf16 *__restrict__ H4, const float *__restrict__ dY, int64_t B,
+                             float *gW5, float *gb5)
+{
+    const int n = threadIdx.x;  // 256 threads
+    const int64_t b0 = (int64_t)blockIdx.x * 256;
+    __shared__ float sdy[256][NOUT];
+    for (int i = n; i < 256 * NOUT; i += 256) {
+        const int64_t b = b0 + i / NOUT;
+        sdy[i / NOUT][i % NOUT] = (b < B) ? dY[b * NOUT + i % NOUT] : 0.f;
+    }
+    __syncthreads();
+    float acc[NOUT] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = 0; r < 256 && b0 + r < B; ++r) {
+        const float h = bfv(H4, (b0 + r) * HID + n);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) acc[o] += h * sdy[r][o];
+    }
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) atomicAdd(&gW5[n * NOUT + o], acc[o]);
+    if (n < NOUT) {
+        float s = 0.f;
+        for (int r = 0; r < 256 && b0 + r < B; ++r) s += sdy[r][n];
+        atomicAdd(&gb5[n], s);
+    }
+}
+
+// Bias gradient of a hidden layer: gb[n] += sum_b dZ[b][n] (256 rows per block).
+__global__ void bias_grad(const bf16 *__restrict__ dZ, int64_t B, float *gb)
+{
+    const int n = threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.x * 256;
+    float s = 0.f;
+    for (int r = 0; r < 256 && b0 + r < B; ++r) s += bfv(dZ, (b0 + r) * HID + n);
+    atomicAdd(&gb[n], s);
+}
+
+// Layer-1 weight gradient: gW1[k][n] += sum_b x[b][k] dZ1[b][n].
+__global__ void layer1_bwd_w(const float *__restrict__ x, const bf16 *__restrict__ dZ1, int64_t B,
+                             float *gW1)
+{
+    const int n = threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.x * 256;
+    float acc[NIN] = {0.f, 0.f, 0.f, 0.f};
+    for (int r = 0; r < 256 && b0 + r < B; ++r) {
+        const float d = bfv(dZ1, (b0 + r) * HID + n);
+#pragma unroll
+        for (int k = 0; k < NIN; ++k) acc[k] += x[(b0 + r) * NIN + k] * d;
+    }
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) atomicAdd(&gW1[k * HID + n], acc[k]);
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master weights; refreshes the BF16 copy.
+__global__ void adam_step(float *p, bf16 *pb, const float *g, float *m1, float *m2, int n,
+                          float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float w = p[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    p[i] = w;
+    pb[i] = __float2bfloat16_rn(w);
+}
+
+__global__ void to_bf16(const float *p, bf16 *pb, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// Deterministic initialisation: counter-based hash -> uniform in [-s, s], s = 1/sqrt(fan_in).
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+__global__ void init_params(float *p, bf16 *pb, uint64_t seed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAM) return;
+    int fan_in;
+    bool bias;
+    if (i < OFF_B1) { fan_in = NIN; bias = false; }
+    else if (i < OFF_W2) { fan_in = NIN; bias = true; }
+    else if (i < OFF_W5) {
+        const int r = (i - OFF_W2) % LAYER_SZ;
+        fan_in = HID;
+        bias = r >= HID * HID;
+    } else { fan_in = HID; bias = i >= OFF_B5; }
+    const double u = (double)(mix64(seed ^ (uint64_t)i * 0x2545f4914f6cdd1dULL) >> 11) * 0x1.0p-53;
+    const float w = bias ? 0.f : (float)((2.0 * u - 1.0) / sqrt((double)fan_in));
+    p[i] = w;
+    pb[i] = __float2bfloat16_rn(w);
+}
+
+// ---- training targets from traced rays -----------------------------------------------------
+// x = (alpha/20, beta/20, a, cos i); t = (captured, log r, phi/pi, g, mask_cross, mask_g, 0, 0)
+// where (r, phi) is the disk hit for rays that stop on the disk, else the first crossing if
+// r <= r_max; g is defined on disk hits.
+__global__ void make_targets(const odx_ray_record *__restrict__ rec, const double *__restrict__ rays,
+                             int64_t n, int64_t n_pad, double r_max, float *x, float *t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    float xv[4] = {0.f, 0.f, 0.f, 0.f}, tv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (i < n) {
+        const double *r4 = rays + 4 * i;
+        xv[0] = (float)(r4[0] / 20.0);
+        xv[1] = (float)(r4[1] / 20.0);
+        xv[2] = (float)r4[2];
+        xv[3] = (float)r4[3];
+        const odx_ray_record &R = rec[i];
+        tv[0] = (R.status == ODX_CAPTURED) ? 1.f : 0.f;
+        if (R.status == ODX_DISK_HIT) {
+            tv[1] = (float)log(R.r_hit);
+            tv[2] = (float)(R.phi_hit / M_PI);
+            tv[3] = (float)R.g;
+            tv[4] = 1.f;
+            tv[5] = 1.f;
+        } else if (R.n_cross >= 1 && R.r_cross <= r_max && R.status != ODX_CAPTURED) {
+            tv[1] = (float)log(R.r_cross);
+            tv[2] = (float)(R.phi_cross / M_PI);
+            tv[4] = 1.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[i * 4 + k] = xv[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t[i * 8 + k] = tv[k];
+}
+
+// ---- surrogate render ---------------------------------------------------------------------
+constexpr int BCRIT_N = 4096;
+
+// Critical curve of Kerr (Bardeen 1973): spherical photon orbits at r in [r_pro, r_ret] with
+// xi = L/E, eta = Q/E^2; image-plane point alpha = -xi / sin i, beta = +-sqrt(eta + a^2 cos^2 i
+// - xi^2 cot^2 i).  Table: for BCRIT_N polar angles psi in [-pi, pi), the radius b_c(psi).
+__global__ void bcrit_table(double a, double inc, double r_in_scene, float *tab)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) tab[BCRIT_N] = (float)(r_in_scene > 0.0 ? r_in_scene : isco_radius(a));
+    if (j >= BCRIT_N) return;
+    const double psi = -M_PI + (j + 0.5) * (2.0 * M_PI / BCRIT_N);
+    if (fabs(a) < 1e-6) {
+        tab[j] = (float)(3.0 * sqrt(3.0));
+        return;
+    }
+    const double si = fmax(sin(inc), 1e-6), ci = cos(inc);
+    const double r_pro = 2.0 * (1.0 + cos(2.0 / 3.0 * acos(-a)));
+    const double r_ret = 2.0 * (1.0 + cos(2.0 / 3.0 * acos(a)));
+    const double sgn = psi >= 0.0 ? 1.0 : -1.0;  // upper or lower half
+    const double target = fabs(psi);             // angle from +alpha on that half, in [0, pi]
+    // along r the upper-half angle decreases from ~pi (prograde side) to ~0 (retrograde side);
+    // bisect on r over the part of the curve that is visible (beta^2 >= 0)
+    auto point = [&](double r, double &al, double &be2) {
+        const double xi = (r * r * (3.0 - r) - a * a * (r + 1.0)) / (a * (r - 1.0));
+        const double eta = r * r * r * (4.0 * a * a - r * (r - 3.0) * (r - 3.0)) /
+                           (a * a * (r - 1.0) * (r - 1.0));
+        al = -xi / si;
+        be2 = eta + a * a * ci * ci - xi * xi * ci * ci / (si * si);
+    };
+    double lo = r_pro, hi = r_ret;
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        double al, be2;
+        point(mid, al, be2);
+        const double ang = atan2(sqrt(fmax(be2, 0.0)), al);
+        if (ang > target) lo = mid; else hi = mid;
+    }
+    double al, be2;
+    point(0.5 * (lo + hi), al, be2);
+    (void)sgn;
+    tab[j] = (float)sqrt(al * al + fmax(be2, 0.0));
+}
+
+__global__ void surrogate_inputs(const DevScene *S, int64_t n_pad, float *x)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pad) return;
+    const odx_scene &s = S->s;
+    const int64_t n = (int64_t)s.n_alpha * s.n_beta;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (p < n) {
+        const int64_t i = p % s.n_alpha, j = p / s.n_alpha;
+        const double al = s.alpha_min + (((double)i + 0.5) * (s.alpha_max - s.alpha_min)) / s.n_alpha;
+        const double be = s.beta_min + (((double)j + 0.5) * (s.beta_max - s.beta_min)) / s.n_beta;
+        v[0] = (float)(al / 20.0);
+        v[1] = (float)(be / 20.0);
+        v[2] = (float)s.a;
+        v[3] = (float)cos(s.theta_obs);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[p * 4 + k] = v[k];
+}
+
+// Per pixel: fallback if |b - b_c(psi)| < band or the capture probability is in [p_lo, p_hi];
+// otherwise the surrogate's thin-disk intensity.  Fallback pixels are compacted per warp
+// (ballot, one atomicAdd per warp) into a ray list and a pixel list.
+__global__ void surrogate_classify(const DevScene *S, const float *__restrict__ y,
+                                   const float *__restrict__ tab, double band, float p_lo,
+                                   float p_hi, double *image, double *fb_rays, int64_t *fb_pix,
+                                   unsigned long long *fb_count)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const odx_scene &s = S->s;
+    const int64_t n = (int64_t)s.n_alpha * s.n_beta;
+    bool fb = false;
+    double al = 0.0, be = 0.0;
+    if (p < n) {
+        const int64_t i = p % s.n_alpha, j = p / s.n_alpha;
+        al = s.alpha_min + (((double)i + 0.5) * (s.alpha_max - s.alpha_min)) / s.n_alpha;
+        be = s.beta_min + (((double)j + 0.5) * (s.beta_max - s.beta_min)) / s.n_beta;
+        const float *yp = y + p * 4;
+        const float prob = 1.f / (1.f + __expf(-yp[0]));
+        const float alf = (float)al, bef = (float)be;
+        const float psi = atan2f(bef, alf);
+        int k = (int)floorf((psi + (float)M_PI) / (2.f * (float)M_PI) * BCRIT_N);
+        k = min(max(k, 0), BCRIT_N - 1);
+        const float b = sqrtf(alf * alf + bef * bef);
+        fb = fabsf(b - tab[k]) < (float)band || (prob >= p_lo && prob <= p_hi);
+        float I = 0.f;
+        if (!fb && prob < 0.5f) {
+            const float r = __expf(yp[1]);
+            if (r >= tab[BCRIT_N] && r <= (float)s.r_out) {
+                const float g = yp[3];
+                I = g * g * g * g * __powf(r, -(float)s.q_emis);
+            }
+        }
+        image[p] = fb ? 0.0 : (double)I;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, fb);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(fb_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (fb) {
+        const unsigned long long slot = base + __popc(m & ((1u << lane) - 1u));
+        fb_rays[4 * slot + 0] = al;
+        fb_rays[4 * slot + 1] = be;
+        fb_rays[4 * slot + 2] = s.a;
+        fb_rays[4 * slot + 3] = cos(s.theta_obs);
+        fb_pix[slot] = p;
+    }
+}
+
+__global__ void scatter_fallback(const odx_ray_record *__restrict__ rec,
+                                 const int64_t *__restrict__ pix, int64_t m, double *image)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) image[pix[j]] = rec[j].intensity;
+}
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <bool A_T, bool B_T, int EPI>
+void gemm(const bf16 *A, const bf16 *B, int M, int N, int K, int lda, int ldb, int splits,
+          EpiArgs ep, cudaStream_t st)
+{
+    const int kps = ((K / splits + BK - 1) / BK) * BK;
+    dim3 grid(N / BN, M / BM, (K + kps - 1) / kps);
+    gemm_bf16_kernel<A_T, B_T, EPI><<<grid, GEMM_THREADS, 0, st>>>(A, B, M, N, K, lda, ldb, kps, ep);
+}
+
+// Forward pass over B rows (B multiple of 128).  With t: loss and dL/dy as well.
+void forward(odx_mlp *m, const float *x, int64_t B, int64_t B_true, float *Y, const float *t,
+             bool keep_z, cudaStream_t st)
+{
+    layer1_fwd<<<blocks_for(B * HID, 256), 256, 0, st>>>(x, m->pb, m->p, B,
+                                                       keep_z ? m->Z[1] : nullptr, m->H[1]);
+    for (int l = 2; l <= 4; ++l) {
+        EpiArgs ep{};
+        ep.bias = m->p + off_b(l);
+        ep.Z = keep_z ? m->Z[l] : nullptr;
+        ep.H = m->H[l];
+        ep.ldc = HID;
+        gemm<false, false, EPI_BIAS_SILU>(m->H[l - 1], m->pb + off_w(l), (int)B, HID, HID, HID,
+                                          HID, 1, ep, st);
+    }
+    layer5_fwd_loss<<<blocks_for(B * 32, 256), 256, 0, st>>>(m->H[4], m->pb, m->p, B, B_true, Y,
+                                                             t, m->dY, m->loss);
+}
+
+// Backward pass after forward(..., keep_z = true, t): gradients into m->grad (zeroed here).
+void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
+{
+    cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float), st);
+    const unsigned rblocks = blocks_for(B, 256);
+    layer5_bwd_w<<<rblocks, 256, 0, st>>>(m->H[4], m->dY, B, m->grad + OFF_W5, m->grad + OFF_B5);
+    layer5_bwd_dz<<<blocks_for(B * HID, 256), 256, 0, st>>>(m->dY, m->pb, m->Z[4], B, m->dZ);
+    bf16 *dz = m->dZ, *dz_prev = m->dZ2;
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
+    for (int l = 4; l >= 2; --l) {
+        // dW_l += H_{l-1}^T dZ_l (split-K over the batch), db_l += sum dZ_l
+        EpiArgs ew{};
+        ew.C32 = m->grad + off_w(l);
+        ew.ldc = HID;
+        gemm<true, false, EPI_ATOMIC_F32>(m->H[l - 1], dz, HID, HID, (int)B, HID, HID, splits, ew, st);
+        bias_grad<<<rblocks, 256, 0, st>>>(dz, B, m->grad + off_b(l));
+        // dZ_{l-1} = (dZ_l W_l^T) * silu'(Z_{l-1})
+        EpiArgs ed{};
+        ed.Z = m->Z[l - 1];
+        ed.H = dz_prev;
+        ed.ldc = HID;
+        gemm<false, true, EPI_DSILU>(dz, m->pb + off_w(l), (int)B, HID, HID, HID, HID, 1, ed, st);
+        std::swap(dz, dz_prev);
+    }
+    layer1_bwd_w<<<rblocks, 256, 0, st>>>(x, dz, B, m->grad + OFF_W1);
+    bias_grad<<<rblocks, 256, 0, st>>>(dz, B, m->grad + OFF_B1);
+}
+
+void free_mlp(odx_mlp *m)
+{
+    cudaSetDevice(m->device);
+    for (void *q : {(void *)m->p, (void *)m->pb, (void *)m->grad, (void *)m->m1, (void *)m->m2,
+                    (void *)m->dZ, (void *)m->dZ2, (void *)m->Y, (void *)m->dY, (void *)m->loss,
+                    (void *)m->xin, (void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays,
+                    (void *)m->fb_pix, (void *)m->fb_count, (void *)m->bcrit,
+                    (void *)m->scene_tab})
+        if (q) cudaFree(q);
+    for (int l = 1; l <= 4; ++l) {
+        if (m->Z[l]) cudaFree(m->Z[l]);
+        if (m->H[l]) cudaFree(m->H[l]);
+    }
+    delete m;
+}
+
+int64_t round128(int64_t n) { return (n + 127) / 128 * 128; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp **out)
+{
+    if (!ctx || !out || max_batch < 1 || max_batch > (int64_t)1 << 22) return ODX_ERR_INVALID_ARG;
+    *out = nullptr;
+    CtxView v;
+    if (ctx_view(ctx, &v) != ODX_OK) return ODX_ERR_INVALID_ARG;
+    if (cudaSetDevice(v.device) != cudaSuccess) return ODX_ERR_CUDA;
+    odx_mlp *m = new odx_mlp();
+    m->ctx = ctx;
+    m->device = v.device;
+    m->max_batch = round128(max_batch);
+    const size_t act = (size_t)m->max_batch * HID * sizeof(bf16);
+    bool ok = cudaMalloc(&m->p, NPARAM * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->pb, NPARAM * sizeof(bf16)) == cudaSuccess &&
+              cudaMalloc(&m->grad, NPARAM * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->m1, NPARAM * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->m2, NPARAM * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->dZ, act) == cudaSuccess && cudaMalloc(&m->dZ2, act) == cudaSuccess &&
+              cudaMalloc(&m->Y, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->dY, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->xin, m->max_batch * NIN * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->bcrit, (BCRIT_N + 1) * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->scene_tab, sizeof(DevScene)) == cudaSuccess &&
+              cudaMalloc(&m->fb_count, sizeof(unsigned long long)) == cudaSuccess;
+    for (int l = 1; l <= 4 && ok; ++l)
+        ok = cudaMalloc(&m->Z[l], act) == cudaSuccess && cudaMalloc(&m->H[l], act) == cudaSuccess;
+    if (!ok) {
+        free_mlp(m);
+        return ODX_ERR_CUDA;
+    }
+    cudaMemset(m->m1, 0, NPARAM * sizeof(float));
+    cudaMemset(m->m2, 0, NPARAM * sizeof(float));
+    init_params<<<blocks_for(NPARAM, 256), 256>>>(m->p, m->pb, seed);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_mlp(m);
+        return ODX_ERR_CUDA;
+    }
+    *out = m;
+    return ODX_OK;
+}
+
+int32_t odx_mlp_destroy(odx_mlp *m)
+{
+    if (m) free_mlp(m);
+    return ODX_OK;
+}
+
+int32_t odx_mlp_get_params(odx_mlp *m, float *host)
+{
+    if (!m || !host) return ODX_ERR_INVALID_ARG;
+    MLP_CUDA(cudaSetDevice(m->device));
+    MLP_CUDA(cudaMemcpy(host, m->p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    return ODX_OK;
+}
+
+int32_t odx_mlp_set_params(odx_mlp *m, const float *host)
+{
+    if (!m || !host) return ODX_ERR_INVALID_ARG;
+    MLP_CUDA(cudaSetDevice(m->device));
+    MLP_CUDA(cudaMemcpy(m->p, host, NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+    to_bf16<<<blocks_for(NPARAM, 256), 256>>>(m->p, m->pb, NPARAM);
+    MLP_CUDA(cudaMemset(m->m1, 0, NPARAM * sizeof(float)));
+    MLP_CUDA(cudaMemset(m->m2, 0, NPARAM * sizeof(float)));
+    m->step = 0;
+    MLP_CUDA(cudaDeviceSynchronize());
+    return ODX_OK;
+}
+
+int32_t odx_mlp_forward(odx_mlp *m, const float *x, int64_t n, float *y, void *stream)
+{
+    if (!m || n < 0 || (n > 0 && (!x || !y))) return ODX_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    MLP_CUDA(cudaSetDevice(m->device));
+    for (int64_t b0 = 0; b0 < n; b0 += m->max_batch) {
+        const int64_t nb = std::min<int64_t>(m->max_batch, n - b0);
+        const int64_t B = round128(nb);
+        MLP_CUDA(cudaMemsetAsync(m->xin, 0, B * NIN * sizeof(float), st));
+        MLP_CUDA(cudaMemcpyAsync(m->xin, x + b0 * NIN, nb * NIN * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st));
+        forward(m, m->xin, B, nb, m->Y, nullptr, false, st);
+        MLP_CUDA(cudaMemcpyAsync(y + b0 * NOUT, m->Y, nb * NOUT * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, st));
+    }
+    MLP_CUDA(cudaGetLastError());
+    return ODX_OK;
+}
+
+int32_t odx_mlp_gradients(odx_mlp *m, const float *x, const float *t, int64_t n, float *grad_host,
+                          float *loss_host)
+{
+    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0) return ODX_ERR_INVALID_ARG;
+    MLP_CUDA(cudaSetDevice(m->device));
+    MLP_CUDA(cudaMemset(m->loss, 0, sizeof(float)));
+    forward(m, x, n, n, m->Y, t, true, nullptr);
+    backward(m, x, n, nullptr);
+    MLP_CUDA(cudaDeviceSynchronize());
+    if (grad_host)
+        MLP_CUDA(cudaMemcpy(grad_host, m->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss_host) MLP_CUDA(cudaMemcpy(loss_host, m->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return ODX_OK;
+}
+
+int32_t odx_mlp_train_step(odx_mlp *m, const float *x, const float *t, int64_t n, float lr,
+                           float *loss_dev, void *stream)
+{
+    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || !(lr > 0.f))
+        return ODX_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    MLP_CUDA(cudaSetDevice(m->device));
+    MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+    forward(m, x, n, n, m->Y, t, true, st);
+    backward(m, x, n, st);
+    m->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+    adam_step<<<blocks_for(NPARAM, 256), 256, 0, st>>>(m->p, m->pb, m->grad, m->m1, m->m2, NPARAM,
+                                                       lr, b1, b2, 1e-8f, c1, c2);
+    if (loss_dev)
+        MLP_CUDA(cudaMemcpyAsync(loss_dev, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    MLP_CUDA(cudaGetLastError());
+    return ODX_OK;
+}
+
+int32_t odx_mlp_targets(odx_ctx *ctx, const odx_ray_record *rec, const double *rays, int64_t n,
+                        double r_max, float *x, float *t, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!rec || !rays || !x || !t))) return ODX_ERR_INVALID_ARG;
+    if (n == 0) return ODX_OK;
+    const int64_t n_pad = round128(n);
+    make_targets<<<blocks_for(n_pad, 256), 256, 0, (cudaStream_t)stream>>>(rec, rays, n, n_pad,
+                                                                           r_max, x, t);
+    MLP_CUDA(cudaGetLastError());
+    return ODX_OK;
+}
+
+int32_t odx_surrogate_render(odx_mlp *m, const odx_scene *scene, double band, double p_lo,
+                             double p_hi, odx_ray_record *fb_records, int64_t *fb_pixels,
+                             double *image, int64_t *n_fallback, void *stream)
+{
+    if (!m || !scene || !fb_records || !image || !(band >= 0.0) || !(p_lo <= p_hi))
+        return ODX_ERR_INVALID_ARG;
+    if (validate_scene_table(scene, 1) != ODX_OK || scene->emitter != ODX_EMIT_THIN_DISK)
+        return ODX_ERR_INVALID_ARG;
+    if (((uintptr_t)fb_records & 15u) != 0) return ODX_ERR_INVALID_ARG;
+    CtxView v;
+    if (ctx_view(m->ctx, &v) != ODX_OK) return ODX_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    MLP_CUDA(cudaSetDevice(m->device));
+    const int64_t n = (int64_t)scene->n_alpha * scene->n_beta;
+    const int64_t n_pad = round128(n);
+    if (m->surr_cap < n_pad) {
+        for (void *q : {(void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays, (void *)m->fb_pix})
+            if (q) cudaFree(q);
+        m->surr_x = m->surr_y = nullptr;
+        m->fb_rays = nullptr;
+        m->fb_pix = nullptr;
+        m->surr_cap = 0;
+        MLP_CUDA(cudaMalloc(&m->surr_x, n_pad * NIN * sizeof(float)));
+        MLP_CUDA(cudaMalloc(&m->surr_y, n_pad * NOUT * sizeof(float)));
+        MLP_CUDA(cudaMalloc(&m->fb_rays, n_pad * 4 * sizeof(double)));
+        MLP_CUDA(cudaMalloc(&m->fb_pix, n_pad * sizeof(int64_t)));
+        m->surr_cap = n_pad;
+    }
+    DevScene d;
+    fill_dev_scene(d, *scene, 0, n, 0);
+    MLP_CUDA(cudaMemcpyAsync(m->scene_tab, &d, sizeof(DevScene), cudaMemcpyHostToDevice, st));
+    MLP_CUDA(cudaMemsetAsync(m->fb_count, 0, sizeof(unsigned long long), st));
+    bcrit_table<<<blocks_for(BCRIT_N, 128), 128, 0, st>>>(scene->a, scene->theta_obs, scene->r_in,
+                                                          m->bcrit);
+    surrogate_inputs<<<blocks_for(n_pad, 256), 256, 0, st>>>(m->scene_tab, n_pad, m->surr_x);
+    for (int64_t b0 = 0; b0 < n_pad; b0 += m->max_batch) {
+        const int64_t B = std::min<int64_t>(m->max_batch, n_pad - b0);
+        forward(m, m->surr_x + b0 * NIN, B, B, m->surr_y + b0 * NOUT, nullptr, false, st);
+    }
+    surrogate_classify<<<blocks_for(n, 256), 256, 0, st>>>(m->scene_tab, m->surr_y, m->bcrit, band,
+                                                          (float)p_lo, (float)p_hi, image,
+                                                          m->fb_rays, m->fb_pix, m->fb_count);
+    unsigned long long nfb = 0;
+    MLP_CUDA(cudaMemcpyAsync(&nfb, m->fb_count, sizeof(nfb), cudaMemcpyDeviceToHost, st));
+    MLP_CUDA(cudaStreamSynchronize(st));
+    if (n_fallback) *n_fallback = (int64_t)nfb;
+    if (nfb > 0) {
+        // trace the fallback pixels (list mode, the scene's own precision) and scatter them
+        fill_dev_scene(d, *scene, 0, (int64_t)nfb, 0);
+        MLP_CUDA(cudaMemcpyAsync(m->scene_tab, &d, sizeof(DevScene), cudaMemcpyHostToDevice, st));
+        MLP_CUDA(cudaMemsetAsync(v.queue, 0, sizeof(unsigned long long), st));
+        TraceArgs a{};
+        a.scenes = m->scene_tab;
+        a.n_scenes = 1;
+        a.list_mode = 1;
+        a.rays = m->fb_rays;
+        a.n_total = (int64_t)nfb;
+        a.records = fb_records;
+        a.image = nullptr;
+        a.queue = v.queue;
+        a.stats = v.stats;
+        a.chunk = v.launch.chunk;
+        a.persistent = v.launch.persistent;
+        a.fp64_batch = v.launch.fp64_batch;
+        const cudaError_t e = scene->precision == ODX_MIXED
+                                  ? launch_trace_mixed(a, 0, v.launch, v.num_sms, st)
+                                  : launch_trace_fp64(a, 0, v.launch, v.num_sms, st);
+        if (e != cudaSuccess) return ODX_ERR_CUDA;
+        scatter_fallback<<<blocks_for((int64_t)nfb, 256), 256, 0, st>>>(fb_records, m->fb_pix,
+                                                                       (int64_t)nfb, image);
+        if (fb_pixels)
+            MLP_CUDA(cudaMemcpyAsync(fb_pixels, m->fb_pix, nfb * sizeof(int64_t),
+                                     cudaMemcpyDeviceToDevice, st));
+    }
+    MLP_CUDA(cudaGetLastError());
+    return ODX_OK;
+}
+
+}  // extern "C"

@@ -296,6 +296,24 @@ int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes)
 }
 
 int32_t transfer_slots(int32_t emitter, int32_t n_freq) { return nf_slots(emitter, n_freq); }
+
+struct CtxView {
+    int device, num_sms;
+    odx_launch launch;
+    unsigned long long *queue;
+    DevStats *stats;
+};
+// What the learned-surrogate code needs from a context to launch the tracer.
+int32_t ctx_view(odx_ctx *ctx, CtxView *v)
+{
+    if (!ctx || !v) return ODX_ERR_INVALID_ARG;
+    v->device = ctx->device;
+    v->num_sms = ctx->num_sms;
+    v->launch = ctx->launch;
+    v->queue = ctx->queue;
+    v->stats = ctx->stats;
+    return ODX_OK;
+}
 }  // namespace odx
 
 extern "C" {
