@@ -225,6 +225,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         tr.render(scene, out=(rec, img))
     barrier()
+    B.odx_set_kernel_timing(tr.ctx, True)
     tr.stats(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -242,6 +243,8 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     st = tr.stats(reset=True)
+    B.odx_set_kernel_timing(tr.ctx, False)
+    kernel_ms = st["trace_ms"] / max(1, st["trace_launches"])
     total_ms = sum(times)
     steps_local = st["steps_accepted"] + st["steps_rejected"]
     t = torch.tensor([total_ms, float(steps_local), float(st["rays"])], dtype=torch.float64,
@@ -258,8 +261,8 @@ def run_ours(args):
 
     # roofline of the tracing kernel (the only kernel of the step)
     peak = B.odx_fma_peak(tr.ctx, "fp64" if args.precision == "fp64" else "mixed")
-    flops = flops_per_step(scene) * steps_local
-    achieved = flops / (sum(times) * 1e-3)
+    flops = flops_per_step(scene) * steps_local / args.steps  # per launch
+    achieved = flops / (kernel_ms * 1e-3)
     traffic = read_traffic(WORKLOAD if args.size == 512 else None, args.precision)
 
     # the plain FP64 path on the same image: its speed, and the production path's image
@@ -337,6 +340,102 @@ def run_ours(args):
                    "lane_refill_efficiency": sts["lane_active"] / max(1, sts["lane_slots"]),
                    "cuda_graph": True, "autotuned_launch": best}
 
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.mean(out)
+
+    def rel_l1(a, b):
+        return float((a - b).abs().sum() / b.abs().sum())
+
+    # secondary: the learned transfer function (trained here on integrator rays) against the
+    # mixed and FP64 integrators on the 2048^2 thin-disk image at a = 0.7, i = 45 deg
+    surrogate = None
+    if args.surrogate and args.size == 512:
+        from paper_1601_02063_gb300 import workloads as W
+        from paper_1601_02063_gb300.surrogate import Surrogate
+        sg = Surrogate(tr, max_batch=65536)
+        t0 = time.perf_counter()
+        xd, td = sg.make_data(1 << 23)
+        loss = sg.train(xd, td, epochs=40, batch=65536, lr=2e-3, lr_final=2e-5)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del xd, td
+        sc = W.surrogate_scene_2048()
+        n2 = sc["n_alpha"] * sc["n_beta"]
+        rec2, img2 = tr.alloc(n2, n2)
+        tr.render(dict(sc, precision="fp64"), out=(rec2, img2))
+        torch.cuda.synchronize()
+        ref64 = img2[:n2].clone()
+        ms64 = timed(lambda: tr.render(dict(sc, precision="fp64"), out=(rec2, img2)), 1)
+        tr.render(sc, out=(rec2, img2))
+        ms_mixed = timed(lambda: tr.render(sc, out=(rec2, img2)), 3)
+        err_mixed = rel_l1(img2[:n2], ref64)
+        out_s = sg.render(sc)
+        holder = {}
+
+        def surr():
+            holder["r"] = sg.render(sc, out=out_s[:3])
+        ms_s = timed(surr, 3)
+        img_s, _, _, m_fb = holder["r"]
+        surrogate = {
+            "workload": "thin disk 2048x2048, a=0.7, i=45 deg, [-20,20]^2",
+            "training": {"rays": 1 << 23, "steps": len(loss), "seconds": t_train,
+                         "final_loss": float(loss[-20:].mean())},
+            "ms_per_image": ms_s, "images_per_s": 1e3 / ms_s,
+            "fallback_fraction": m_fb / n2, "image_error_vs_fp64": rel_l1(img_s, ref64),
+            "mixed_integrator": {"ms_per_image": ms_mixed, "images_per_s": 1e3 / ms_mixed,
+                                 "image_error_vs_fp64": err_mixed},
+            "fp64_integrator": {"ms_per_image": ms64, "images_per_s": 1e3 / ms64},
+            "mlp_flops_per_image": 2.0 * (4 * 256 + 3 * 256 * 256 + 256 * 4) * n2,
+        }
+        sg.close()
+        del rec2, img2, ref64, out_s
+
+    # secondary: the 4096^2 near-edge-on hard case (a = 0.998, i = 85 deg, 8 frequencies),
+    # mixed precision, with its step-count distribution; accuracy against FP64 on the same
+    # scene at 512^2
+    hard = None
+    if args.hard and args.size == 512:
+        from paper_1601_02063_gb300 import workloads as W
+        hsc = W.torus_hard_4096(precision="mixed")
+        nh = B.n_rays(hsc)
+        rech, imgh = tr.alloc(nh, B.n_image(hsc))
+        tr.render(hsc, out=(rech, imgh))
+        torch.cuda.synchronize()
+        tr.stats(reset=True)
+        ms_h = timed(lambda: tr.render(hsc, out=(rech, imgh)), 1)
+        sth = tr.stats(reset=True)
+        rv = rech[:nh].view(torch.int32)[:, 1:3].sum(dim=1).double()
+        qs = torch.quantile(rv[:: max(1, nh // (1 << 20))], torch.tensor(
+            [0.5, 0.9, 0.99, 0.999], dtype=torch.float64, device=rv.device)).tolist()
+        del rech, imgh
+        small = dict(hsc, n_alpha=512, n_beta=512)
+        recs, imgs = tr.alloc(512 * 512, B.n_image(small))
+        tr.render(dict(small, precision="fp64"), out=(recs, imgs))
+        torch.cuda.synchronize()
+        ref = imgs[:B.n_image(small)].view(8, -1).clone()
+        tr.render(small, out=(recs, imgs))
+        torch.cuda.synchronize()
+        got = imgs[:B.n_image(small)].view(8, -1)
+        errs = ((got - ref).abs().sum(dim=1) / ref.abs().sum(dim=1)).tolist()
+        steps_h = sth["steps_accepted"] + sth["steps_rejected"]
+        hard = {"workload": "torus 4096x4096, a=0.998, i=85 deg, 8 log-spaced nu in [0.25,4]",
+                "precision": "mixed", "ms_per_image": ms_h, "images_per_s": 1e3 / ms_h,
+                "ns_per_photon_step": ms_h * 1e6 / steps_h, "steps_per_photon": steps_h / nh,
+                "steps_per_photon_quantiles_50_90_99_999": qs,
+                "lane_refill_efficiency": sth["lane_active"] / max(1, sth["lane_slots"]),
+                "image_error_vs_fp64_at_512": errs}
+        del recs, imgs, ref
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     rec_h = torch.empty(n * B.RECORD_BYTES // 8, dtype=torch.float64).pin_memory().numpy()
     img_h = torch.empty(B.n_image(scene), dtype=torch.float64).pin_memory().numpy()
@@ -379,10 +478,15 @@ def run_ours(args):
         "fp64_step_fraction": st["steps_fp64"] / max(1, steps_local),
         "lane_refill_efficiency": st["lane_active"] / max(1, st["lane_slots"]),
         "batched": batched,
-        "gpu_launches": args.steps,
+        "surrogate": surrogate,
+        "hard_case": hard,
+        "gpu_launches": args.steps * (3 if args.precision == "mixed" else 1),
+        "tracer_kernel_ms": kernel_ms,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "measured FMA-chain microbenchmark, same run",
+                     "kernel": "trace_mixed_kernel" if args.precision == "mixed"
+                               else "trace_fp64_kernel",
                      "pipe": "fp64" if args.precision == "fp64" else "fp32"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 304,
@@ -412,6 +516,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="omit the 64-scene batched sweep measurement")
+    ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
+                    help="omit training and timing the learned surrogate")
+    ap.add_argument("--no-hard", dest="hard", action="store_false",
+                    help="omit the 4096^2 near-edge-on hard case")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

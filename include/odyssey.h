@@ -131,6 +131,8 @@ typedef struct odx_stats {
     int64_t lane_active;    /* lanes holding a live ray summed over warp iterations */
     int32_t error_flag;     /* nonzero: a kernel met an invalid internal state     */
     int32_t reserved;
+    int64_t trace_launches; /* tracing-kernel launches timed (odx_set_kernel_timing)    */
+    double trace_ms;        /* their summed duration, CUDA events on the launch stream */
 } odx_stats;
 
 typedef struct odx_ctx odx_ctx;
@@ -192,6 +194,10 @@ int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_sc
 
 /* Read (stream-ordered, then synchronised) and optionally reset the device counters. */
 int32_t odx_get_stats(odx_ctx *ctx, void *stream, odx_stats *out, int32_t reset);
+
+/* Time every tracing-kernel launch of this context (CUDA events around the kernel on its
+ * stream, reported by odx_get_stats) when on != 0; off by default.  Not during capture. */
+int32_t odx_set_kernel_timing(odx_ctx *ctx, int32_t on);
 
 /* Wait for `stream` with a deadline; ODX_ERR_TIMEOUT if it has not finished in timeout_s
  * seconds (the work keeps running), ODX_ERR_DEVICE_FLAG if a kernel raised its flag. */

@@ -63,7 +63,8 @@ class odx_stats(C.Structure):
     _fields_ = [("rays", C.c_int64), ("steps_accepted", C.c_int64),
                 ("steps_rejected", C.c_int64), ("steps_fp64", C.c_int64),
                 ("lane_slots", C.c_int64), ("lane_active", C.c_int64),
-                ("error_flag", C.c_int32), ("reserved", C.c_int32)]
+                ("error_flag", C.c_int32), ("reserved", C.c_int32),
+                ("trace_launches", C.c_int64), ("trace_ms", C.c_double)]
 
 
 RECORD_DTYPE = np.dtype([
@@ -91,6 +92,7 @@ _SIGNATURES = [
     ("odx_render_host", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P, _P]),
     ("odx_get_stats", C.c_int32, [_P, _P, C.POINTER(odx_stats), C.c_int32]),
     ("odx_sync", C.c_int32, [_P, _P, C.c_double]),
+    ("odx_set_kernel_timing", C.c_int32, [_P, C.c_int32]),
     ("odx_torus_norm", C.c_double, [C.c_double] * 6),
     ("odx_fma_peak", C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double)]),
     ("odx_render_static", C.c_int32, [C.POINTER(odx_scene), C.c_int32, _P, _P, _P]),
@@ -209,6 +211,10 @@ def odx_get_stats(ctx, stream: int | None = None, reset: bool = False) -> dict:
     s = odx_stats()
     _check(ctx, lib().odx_get_stats(ctx, stream or None, C.byref(s), int(reset)), "odx_get_stats")
     return {f: getattr(s, f) for f, _ in odx_stats._fields_}
+
+
+def odx_set_kernel_timing(ctx, on: bool) -> None:
+    _check(ctx, lib().odx_set_kernel_timing(ctx, int(bool(on))), "odx_set_kernel_timing")
 
 
 def odx_sync(ctx, stream: int | None = None, timeout_s: float = 600.0) -> None:

@@ -19,10 +19,6 @@
 #include "odx_internal.h"
 
 namespace odx {
-cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                               int32_t num_sms, cudaStream_t st);
-cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                              int32_t num_sms, cudaStream_t st);
 int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes);
 void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t n_rays,
                     int64_t img_offset);

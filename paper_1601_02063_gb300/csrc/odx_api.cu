@@ -14,10 +14,6 @@
 #include "odx_internal.h"
 
 namespace odx {
-cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                              int32_t num_sms, cudaStream_t st);
-cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                               int32_t num_sms, cudaStream_t st);
 }  // namespace odx
 
 using namespace odx;
@@ -36,6 +32,10 @@ struct odx_ctx {
     void *hbuf = nullptr;
     size_t hbuf_bytes = 0;
     std::string last_error;
+    // optional per-launch timing of the tracing kernel
+    bool time_kernels = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
 };
 
 namespace {
@@ -138,6 +138,24 @@ int32_t set_device(odx_ctx *ctx)
     return ODX_OK;
 }
 
+// Event pair for timing the next tracing-kernel launch (none when timing is off or the
+// stream is being captured).
+void timing_events(odx_ctx *ctx, cudaStream_t st, cudaEvent_t *e0, cudaEvent_t *e1)
+{
+    *e0 = *e1 = nullptr;
+    if (!ctx->time_kernels) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (ctx->events_used == ctx->events.size()) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+        ctx->events.push_back({a, b});
+    }
+    *e0 = ctx->events[ctx->events_used].first;
+    *e1 = ctx->events[ctx->events_used].second;
+    ++ctx->events_used;
+}
+
 // Validate, build the scene table, copy it and launch.  Shared by the render and list paths.
 int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const double *rays,
                int64_t n_list, odx_ray_record *records, double *image, cudaStream_t st,
@@ -194,9 +212,11 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
+    cudaEvent_t ev0, ev1;
+    timing_events(ctx, st, &ev0, &ev1);
     cudaError_t e = scenes[0].precision == ODX_MIXED
-                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st)
-                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st);
+                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st, ev0, ev1)
+                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st, ev0, ev1);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace kernel launch");
     return ODX_OK;
 }
@@ -245,9 +265,11 @@ int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const odx_scene
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
+    cudaEvent_t ev0, ev1;
+    timing_events(ctx, st, &ev0, &ev1);
     cudaError_t e = scenes[0].precision == ODX_MIXED
-                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st)
-                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st);
+                        ? launch_trace_mixed(a, slots, ctx->launch, ctx->num_sms, st, ev0, ev1)
+                        : launch_trace_fp64(a, slots, ctx->launch, ctx->num_sms, st, ev0, ev1);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "trace kernel launch");
     return ODX_OK;
 }
@@ -370,6 +392,10 @@ int32_t odx_destroy(odx_ctx *ctx)
     if (ctx->scenes) cudaFree(ctx->scenes);
     if (ctx->hbuf) cudaFree(ctx->hbuf);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    for (auto &pr : ctx->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
     delete ctx;
     return ODX_OK;
 }
@@ -468,10 +494,26 @@ int32_t odx_get_stats(odx_ctx *ctx, void *stream, odx_stats *out, int32_t reset)
     out->lane_active = (int64_t)d.active;
     out->error_flag = d.error_flag;
     out->reserved = 0;
+    out->trace_launches = (int64_t)ctx->events_used;
+    out->trace_ms = 0.0;
+    for (size_t i = 0; i < ctx->events_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->events[i].first, ctx->events[i].second) == cudaSuccess)
+            out->trace_ms += ms;
+    }
     if (reset) {
+        ctx->events_used = 0;
         ODX_CUDA(ctx, cudaMemsetAsync(ctx->stats, 0, sizeof(DevStats), st));
         ODX_CUDA(ctx, cudaStreamSynchronize(st));
     }
+    return ODX_OK;
+}
+
+int32_t odx_set_kernel_timing(odx_ctx *ctx, int32_t on)
+{
+    if (!ctx) return ODX_ERR_INVALID_ARG;
+    ctx->time_kernels = on != 0;
+    ctx->events_used = 0;
     return ODX_OK;
 }
 

@@ -49,10 +49,14 @@ struct TraceArgs {
     int32_t pad;
 };
 
-// Launch the tracing kernel matching (emitter, n_freq, precision) on `stream`.
-cudaError_t launch_trace(const TraceArgs &args, int32_t emitter, int32_t n_freq,
-                         int32_t precision, const odx_launch &launch, int32_t num_sms,
-                         cudaStream_t stream);
+// Launch the FP64 or mixed tracer (with its passes) on `stream`; when ev0/ev1 are given,
+// they are recorded immediately before and after the tracing kernel itself.
+cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                              int32_t num_sms, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr);
+cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+                               int32_t num_sms, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                               cudaEvent_t ev1 = nullptr);
 
 // FMA-chain peak microbenchmark: returns flop/s via *flops (synchronous).
 cudaError_t run_fma_peak(int32_t precision, int32_t num_sms, double *flops);

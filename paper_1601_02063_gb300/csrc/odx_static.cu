@@ -19,10 +19,6 @@
 namespace odx {
 int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes);
 int32_t transfer_slots(int32_t emitter, int32_t n_freq);
-cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                              int32_t num_sms, cudaStream_t st);
-cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                               int32_t num_sms, cudaStream_t st);
 }  // namespace odx
 
 namespace {

@@ -244,16 +244,18 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
 }
 
 cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                              int32_t num_sms, cudaStream_t st)
+                              int32_t num_sms, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     const dim3 block(L.block);
     const dim3 grid = trace_grid(args, L, num_sms);
+    if (ev0) cudaEventRecord(ev0, st);
     switch (nf_slots) {
     case 0: trace_fp64_kernel<0><<<grid, block, 0, st>>>(args); break;
     case 4: trace_fp64_kernel<4><<<grid, block, 0, st>>>(args); break;
     case 8: trace_fp64_kernel<8><<<grid, block, 0, st>>>(args); break;
     default: return cudaErrorInvalidValue;
     }
+    if (ev1) cudaEventRecord(ev1, st);
     return cudaGetLastError();
 }
 

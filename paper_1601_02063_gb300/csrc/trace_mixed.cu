@@ -548,7 +548,7 @@ cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 gri
 }
 
 cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
-                               int32_t num_sms, cudaStream_t st)
+                               int32_t num_sms, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     if (L.block > 128) return cudaErrorInvalidValue;
     if (args.n_total <= 0) return cudaSuccess;
@@ -557,6 +557,7 @@ cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const od
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid = trace_grid(args, L, num_sms);
+    if (ev0) cudaEventRecord(ev0, st);
     switch (nf_slots) {
     case 0: e = launch_mixed_nf<0>(args, L, grid, st); break;
     case 4: e = launch_mixed_nf<4>(args, L, grid, st); break;
@@ -564,6 +565,7 @@ cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const od
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (ev1) cudaEventRecord(ev1, st);
     mixed_finish_kernel<<<pass_blocks, 128, 0, st>>>(args);
     return cudaGetLastError();
 }

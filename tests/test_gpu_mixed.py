@@ -146,3 +146,18 @@ def test_mixed_full_size_torus_sampled_pixels(tracer, orc):
         I = img[k * n + pix]
         err = np.abs(I - ref["I_nu"][:, k]).sum() / np.abs(ref["I_nu"][:, k]).sum()
         assert err <= IMG_ERR
+
+
+def test_mixed_eight_frequency_hard_case(tracer, orc):
+    """Hard case (a = 0.998, i = 85 deg, 8 frequencies) at 64x64 in mixed precision: image error
+    per frequency against the FP64 oracle."""
+    sc = W.torus_hard_4096(precision="mixed")
+    sc.update(n_alpha=64, n_beta=64)
+    got, img = _render(tracer, sc)
+    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])))
+    n = 64 * 64
+    assert np.mean(got["status"] != ref["status"]) < STATUS_DISAGREE
+    for k in range(8):
+        I_ref = ref["I_nu"][:, k]
+        err = np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum()
+        assert err <= IMG_ERR, (k, err)

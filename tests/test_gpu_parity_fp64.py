@@ -237,3 +237,17 @@ def test_full_size_torus_sampled_pixels(tracer, orc):
     for k in range(3):
         rel = _rel(img[k * n + pix][same], ref["I_nu"][:, k][same])
         assert np.mean(rel <= REL_INTENSITY) >= 0.99 and rel.max() <= 1e-6
+
+
+def test_eight_frequency_torus_hard_case_small(tracer, orc):
+    """The near-edge-on hard case (a = 0.998, i = 85 deg, 8 log-spaced frequencies in
+    [0.25, 4]) at 40x32: the eight-slot transfer kernels against the oracle."""
+    sc = W.torus_hard_4096(precision="fp64")
+    sc.update(n_alpha=40, n_beta=32)
+    got, img = _render(tracer, sc)
+    ref = orc.render(dict(sc, C_norm=orc.torus_norm(sc["a"])))
+    same = _compare(got, ref, fields=("r_cross",))
+    n = 40 * 32
+    for k in range(8):
+        rel = _rel(img[k * n:(k + 1) * n][same], ref["I_nu"][:, k][same])
+        assert np.mean(rel <= REL_INTENSITY) >= 0.99 and rel.max() <= 1e-5, (k, rel.max())
