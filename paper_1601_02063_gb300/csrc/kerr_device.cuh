@@ -64,9 +64,15 @@ __device__ __forceinline__ void geodesic_rhs(const Geo<T> &g, T r, T th, T pr, T
     const T r2 = r * r, a2 = a * a;
     const T Sig = r2 + a2 * c * c;
     const T Del = r2 - T(2) * r + a2;
-    const T iSD = T(1) / (Sig * Del);
+    T iSD, is;
+    if constexpr (sizeof(T) == 8) {
+        iSD = 1.0 / (Sig * Del);
+        is = 1.0 / s;
+    } else {  // correctly rounded reciprocals without the division slow path
+        iSD = __frcp_rn(Sig * Del);
+        is = __frcp_rn(s);
+    }
     const T iS = Del * iSD;
-    const T is = T(1) / s;
     const T is2 = is * is;
     const T rr = r2 + a2;
     const T P = rr - a * L;

@@ -295,6 +295,7 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
     d.f_ne_index = (float)s.ne_index;
     d.f_inv_2w2 = s.theta_width > 0.0 ? (float)(1.0 / (2.0 * s.theta_width * s.theta_width)) : 0.f;
     d.f_T0 = (float)s.T0;
+    d.f_inv_T0 = s.T0 > 0.0 ? (float)(1.0 / s.T0) : 0.f;
     d.f_T_index = (float)s.T_index;
     d.f_C_norm = (float)s.C_norm;
     d.f_r_out = (float)s.r_out;

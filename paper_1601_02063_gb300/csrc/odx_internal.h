@@ -19,6 +19,7 @@ struct DevScene {
     int64_t pad;
     // FP32 copies of the parameters the FP32 stages read (filled by fill_dev_scene)
     float f_ne_index, f_inv_2w2, f_T0, f_T_index, f_C_norm, f_r_out, f_hmax_frac, f_rtol32;
+    float f_inv_T0, f_pad[3];
     float f_freqs[ODX_MAX_FREQ];
 };
 

@@ -240,6 +240,7 @@ __device__ __forceinline__ MediumT<float> medium32(const DevScene &S, float r_is
     m.ne_index = S.f_ne_index;
     m.inv_2w2 = S.f_inv_2w2;
     m.T0 = S.f_T0;
+    m.inv_T0 = S.f_inv_T0;
     m.T_index = S.f_T_index;
     m.C_norm = S.f_C_norm;
     m.r_isco = r_isco;
@@ -338,6 +339,7 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
         md.ne_index = S.s.ne_index;
         md.inv_2w2 = 1.0 / (2.0 * S.s.theta_width * S.s.theta_width);
         md.T0 = S.s.T0;
+        md.inv_T0 = 1.0 / S.s.T0;
         md.T_index = S.s.T_index;
         md.C_norm = S.s.C_norm;
         md.r_isco = (double)r_isco;

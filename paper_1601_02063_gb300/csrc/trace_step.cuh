@@ -27,11 +27,26 @@ __device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ void m_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
 __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+// correctly rounded reciprocal (FP32: no division slow path) and reciprocal square root
+__device__ __forceinline__ float m_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double m_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float m_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double m_rsqrt(double x) { return 1.0 / sqrt(x); }
+// 1 - exp(-x) for x >= 0 given em = exp(-x): series below 1/32 (the FP32 cancellation
+// there would cost up to 5 bits), expm1 in FP64
+__device__ __forceinline__ float one_minus_exp(float x, float em)
+{
+    return x > 0.03125f ? 1.f - em : x * (1.f - x * (0.5f - x * (1.f / 6.f)));
+}
+__device__ __forceinline__ double one_minus_exp(double x, double em)
+{
+    return x > 0.5 ? 1.0 - em : -expm1(-x);
+}
 
 // Parameters of the analytic torus in the arithmetic type of the step.
 template <typename T>
 struct MediumT {
-    T ne_index, inv_2w2, T0, T_index, C_norm, r_isco;
+    T ne_index, inv_2w2, T0, inv_T0, T_index, C_norm, r_isco;
     T freqs[ODX_MAX_FREQ];
     int n_freq;
 };
@@ -42,6 +57,7 @@ __device__ __forceinline__ void load_medium_t(const DevScene &S, double a, Mediu
     m.ne_index = (T)S.s.ne_index;
     m.inv_2w2 = (T)(1.0 / (2.0 * S.s.theta_width * S.s.theta_width));
     m.T0 = (T)S.s.T0;
+    m.inv_T0 = (T)(1.0 / S.s.T0);
     m.T_index = (T)S.s.T_index;
     m.C_norm = (T)S.s.C_norm;
     m.r_isco = (T)isco_radius(a);
@@ -50,57 +66,76 @@ __device__ __forceinline__ void load_medium_t(const DevScene &S, double a, Mediu
     for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = (T)S.s.freqs[k];
 }
 
-// Analytic torus (see torus_rhs64 for the model): dtau/ds = alpha/g, dI/ds =
-// j/(g nu0^3) exp(-tau) per observed frequency, nu0 = nu_obs / g.
-template <typename T, int NF>
-__device__ __forceinline__ void torus_rhs(const MediumT<T> &m, T a, T L, T r, T th, const T *tau,
-                                          T *ftau, T *fI)
-{
-    T s, c;
-    m_sincos(th, &s, &c);
-    s = fmax(s, T(kSinFloor));
-    const T r2 = r * r, a2 = a * a, s2 = s * s;
-    const T Sig = r2 + a2 * c * c;
-    const T Del = r2 - T(2) * r + a2;
-    const T A = (r2 + a2) * (r2 + a2) - a2 * Del * s2;
-    const T iS = T(1) / Sig;
-    const T gtt = -(T(1) - T(2) * r * iS);
-    const T gtp = -T(2) * a * r * s2 * iS;
-    const T gpp = A * s2 * iS;
-    T Om = T(1) / (r * m_sqrt(r) + a);
-    T N = gtt + T(2) * gtp * Om + gpp * Om * Om;
-    if (!(r >= m.r_isco && N < T(0))) {
-        Om = T(2) * a * r / A;
-        N = gtt + T(2) * gtp * Om + gpp * Om * Om;
-    }
-    const T ig = (T(1) - Om * L) / m_sqrt(-N);  // 1/g = u^t (1 - Omega L), Eq. 2
-    const T lr = m_log(r);
-    const T ne = m_exp(-m.ne_index * lr - c * c * m.inv_2w2);
-    const T iTe = m_exp(m.T_index * lr) / m.T0;
-    const T pref = m.C_norm * ne * ne * m_sqrt(iTe);  // C n_e^2 T^-1/2
-#pragma unroll
-    for (int k = 0; k < NF; ++k) {
-        if (k < m.n_freq) {
-            const T nu0 = m.freqs[k] * ig;
-            const T x = nu0 * iTe;
-            const T em = m_exp(-x);
-            const T om = (x > T(0.5)) ? T(1) - em : -m_expm1(-x);  // 1 - exp(-nu0/T)
-            const T inu3 = T(1) / (nu0 * nu0 * nu0);
-            ftau[k] = T(0.5) * pref * om * inu3 * ig;           // Eq. 30
-            fI[k] = pref * em * inu3 * ig * m_exp(-tau[k]);     // Eq. 31
-        } else {
-            ftau[k] = T(0);
-            fI[k] = T(0);
-        }
-    }
-}
-
+// Geodesic and transfer right-hand sides of one stage together, sharing sin(theta),
+// cos(theta), Sigma, Delta and 1/Sigma between Eqs. 4-15 and the torus model (Eq. 2,
+// Eqs. 30-31): the geodesic part is the same as geodesic_rhs.
 template <typename T, int NF>
 __device__ __forceinline__ void derivs(const Geo<T> &g, const MediumT<T> &m, const T y[6],
-                                       const T *tau, T f[6], T *ft, T *fI)
+                                       const T *tau, T f[6], T *ftau, T *fI)
 {
-    geodesic_rhs<T>(g, y[0], y[1], y[4], y[5], f);
-    if constexpr (NF > 0) torus_rhs<T, NF>(m, g.a, g.L, y[0], y[1], tau, ft, fI);
+    if constexpr (NF == 0) {
+        geodesic_rhs<T>(g, y[0], y[1], y[4], y[5], f);
+    } else {
+        const T r = y[0], pr = y[4], pth = y[5];
+        T s, c;
+        m_sincos(y[1], &s, &c);
+        s = fmax(s, T(kSinFloor));
+        const T a = g.a, L = g.L;
+        const T r2 = r * r, a2 = a * a, s2 = s * s;
+        const T Sig = r2 + a2 * c * c;
+        const T Del = r2 - T(2) * r + a2;
+        const T iSD = m_rcp(Sig * Del);
+        const T iS = Del * iSD;
+        const T iD = Sig * iSD;
+        const T is = m_rcp(s);
+        const T is2 = is * is;
+        const T rr = r2 + a2;
+        const T P = rr - a * L;
+        const T q = L * is - a * s;
+        const T pr2 = pr * pr, pth2 = pth * pth;
+        const T F = Del * pr2 + pth2 + q * q - P * P * iD;
+        const T kap = pth2 + L * L * is2 + a2 * s2;
+        const T rm1 = r - T(1);
+        const T twor = T(2) * r;
+        f[0] = g.sgn * (Del * pr * iS);
+        f[1] = g.sgn * (pth * iS);
+        f[2] = g.sgn * ((twor * a + (Sig - twor) * L * is2) * iSD);
+        f[3] = g.sgn * (T(1) + (twor * rr - twor * a * L) * iSD);
+        f[4] = g.sgn * ((-kap * rm1 + twor * rr - T(2) * a * L) * iSD - T(2) * pr2 * rm1 * iS +
+                        F * (rm1 * iSD + r * iS * iS));
+        f[5] = g.sgn * (s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS);
+
+        // torus: Keplerian flow where r >= r_ISCO and timelike, else ZAMO; g from Eq. 2
+        const T A = rr * rr - a2 * Del * s2;
+        const T gtt = -(T(1) - twor * iS);
+        const T gtp = -twor * a * s2 * iS;
+        const T gpp = A * s2 * iS;
+        T Om = m_rcp(r * m_sqrt(r) + a);
+        T N = gtt + T(2) * gtp * Om + gpp * Om * Om;
+        if (!(r >= m.r_isco && N < T(0))) {
+            Om = twor * a * m_rcp(A);
+            N = gtt + T(2) * gtp * Om + gpp * Om * Om;
+        }
+        const T ig = (T(1) - Om * L) * m_rsqrt(-N);  // 1/g = u^t (1 - Omega L)
+        const T lr = m_log(r);
+        const T ne = m_exp(-m.ne_index * lr - c * c * m.inv_2w2);
+        const T iTe = m_exp(m.T_index * lr) * m.inv_T0;
+        const T pref = m.C_norm * ne * ne * m_sqrt(iTe);  // C n_e^2 T^-1/2
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            if (k < m.n_freq) {
+                const T nu0 = m.freqs[k] * ig;
+                const T x = nu0 * iTe;
+                const T em = m_exp(-x);
+                const T inu3 = m_rcp(nu0 * nu0 * nu0);
+                ftau[k] = T(0.5) * pref * one_minus_exp(x, em) * inu3 * ig;  // Eq. 30
+                fI[k] = pref * em * inu3 * ig * m_exp(-tau[k]);              // Eq. 31
+            } else {
+                ftau[k] = T(0);
+                fI[k] = T(0);
+            }
+        }
+    }
 }
 
 // Right-hand side evaluated out of line and returned by value: one copy of its code serves
@@ -119,8 +154,8 @@ __device__ __noinline__ DerivOut<T, NF> derivs_call(Geo<T> g, MediumT<T> m, T r,
                                                     TauIn<T, NF> tau)
 {
     DerivOut<T, NF> o;
-    geodesic_rhs<T>(g, r, th, pr, pth, o.f);
-    if constexpr (NF > 0) torus_rhs<T, NF>(m, g.a, g.L, r, th, tau.t, o.ft, o.fI);
+    const T y[6] = {r, th, T(0), T(0), pr, pth};
+    derivs<T, NF>(g, m, y, tau.t, o.f, o.ft, o.fI);
     return o;
 }
 
