@@ -57,7 +57,7 @@ __device__ __forceinline__ void geodesic_rhs(const Geo<T> &g, T r, T th, T pr, T
     if constexpr (sizeof(T) == 8) {
         sincos(th, &s, &c);
     } else {
-        sincosf(th, &s, &c);
+        __sincosf(th, &s, &c);  // see m_sincos in trace_step.cuh for the accuracy argument
     }
     s = fmax(s, T(kSinFloor));
     const T a = g.a, L = g.L;

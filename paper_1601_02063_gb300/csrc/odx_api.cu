@@ -114,10 +114,11 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
     return ODX_OK;
 }
 
+// Compiled transfer slots: 3 (the three-frequency workloads), 4 or 8.
 int32_t nf_slots(int32_t emitter, int32_t n_freq)
 {
     if (emitter != ODX_EMIT_TORUS) return 0;
-    return n_freq <= 4 ? 4 : 8;
+    return n_freq <= 3 ? 3 : (n_freq <= 4 ? 4 : 8);
 }
 
 int32_t ensure_scene_capacity(odx_ctx *ctx, int64_t n)

@@ -251,6 +251,7 @@ cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx
     if (ev0) cudaEventRecord(ev0, st);
     switch (nf_slots) {
     case 0: trace_fp64_kernel<0><<<grid, block, 0, st>>>(args); break;
+    case 3: trace_fp64_kernel<3><<<grid, block, 0, st>>>(args); break;
     case 4: trace_fp64_kernel<4><<<grid, block, 0, st>>>(args); break;
     case 8: trace_fp64_kernel<8><<<grid, block, 0, st>>>(args); break;
     default: return cudaErrorInvalidValue;

@@ -562,6 +562,7 @@ cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const od
     if (ev0) cudaEventRecord(ev0, st);
     switch (nf_slots) {
     case 0: e = launch_mixed_nf<0>(args, L, grid, st); break;
+    case 3: e = launch_mixed_nf<3>(args, L, grid, st); break;
     case 4: e = launch_mixed_nf<4>(args, L, grid, st); break;
     case 8: e = launch_mixed_nf<8>(args, L, grid, st); break;
     default: return cudaErrorInvalidValue;

@@ -25,7 +25,10 @@ __device__ __forceinline__ float m_cos(float x) { return cosf(x); }
 __device__ __forceinline__ double m_cos(double x) { return cos(x); }
 __device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
-__device__ __forceinline__ void m_sincos(float x, float *s, float *c) { sincosf(x, s, c); }
+// FP32 stages: the hardware sine/cosine (absolute error <= 2^-21.4 for |x| <= pi, theta stays
+// in [0, pi] up to pole passages) is well inside the stages' 1e-6 tolerance; measured
+// image error vs FP64 changes by 1 % of itself.  Crossing tests keep the accurate cosf.
+__device__ __forceinline__ void m_sincos(float x, float *s, float *c) { __sincosf(x, s, c); }
 __device__ __forceinline__ void m_sincos(double x, double *s, double *c) { sincos(x, s, c); }
 // correctly rounded reciprocal (FP32: no division slow path) and reciprocal square root
 __device__ __forceinline__ float m_rcp(float x) { return __frcp_rn(x); }
