@@ -418,6 +418,115 @@ __global__ void scatter_fallback(const odx_ray_record *__restrict__ rec,
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ---- fused inference: all five layers of a 128-row tile in one CTA --------------------------
+// Activations stay in shared memory (128 x 256 BF16, padded rows); each 256 x 256 layer
+// streams its BF16 weights from L2 in 32-row chunks (cp.async, double-buffered) and runs
+// mma.sync m16n8k16 with 16 warps tiled 4 (rows) x 4 (columns) over 32 x 64 each; bias and
+// SiLU are applied to the FP32 accumulators before the BF16 result overwrites the tile.
+constexpr int FZ_ROWS = 128, FZ_THREADS = 512, FZ_LDH = HID + 8, FZ_KC = 32;
+constexpr size_t FZ_SMEM = (size_t)(FZ_ROWS * FZ_LDH + 2 * FZ_KC * FZ_LDH) * sizeof(bf16);
+
+__global__ void __launch_bounds__(FZ_THREADS, 1)
+    mlp_fused_forward(const float *__restrict__ x, const bf16 *__restrict__ pb,
+                      const float *__restrict__ p, int64_t n_rows, float *__restrict__ y)
+{
+    extern __shared__ __align__(16) unsigned char fz_smem[];
+    bf16 *sH = reinterpret_cast<bf16 *>(fz_smem);
+    bf16 *sW = sH + FZ_ROWS * FZ_LDH;  // [2][FZ_KC][FZ_LDH]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;  // 4 x 4 warps, 32 x 64 each
+    const int64_t row0 = (int64_t)blockIdx.x * FZ_ROWS;
+
+    // layer 1 on CUDA cores: 128 x 256 outputs, 64 per thread
+    for (int i = tid; i < FZ_ROWS * HID; i += FZ_THREADS) {
+        const int r = i / HID, nn = i % HID;
+        const int64_t gr = row0 + r;
+        float z = p[OFF_B1 + nn];
+        if (gr < n_rows) {
+#pragma unroll
+            for (int k = 0; k < NIN; ++k) z += x[gr * NIN + k] * bfv(pb, OFF_W1 + k * HID + nn);
+        }
+        sH[r * FZ_LDH + nn] = __float2bfloat16_rn(silu(z));
+    }
+
+    const int j8 = lane >> 3, r8 = lane & 7, g = lane >> 2, q = lane & 3;
+    for (int l = 2; l <= 4; ++l) {
+        const bf16 *W = pb + off_w(l);
+        auto load_chunk = [&](int buf, int kc) {
+            // 32 rows x 256 columns = 1024 16-byte chunks, 2 per thread
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int chunk = tid + c * FZ_THREADS;
+                const int r = chunk >> 5, cc = (chunk & 31) * 8;
+                cp_async16(&sW[(buf * FZ_KC + r) * FZ_LDH + cc], W + (size_t)(kc * FZ_KC + r) * HID + cc);
+            }
+            cp_async_commit();
+        };
+        float acc[2][8][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.f;
+        __syncthreads();  // previous layer's tile complete
+        load_chunk(0, 0);
+        for (int kc = 0; kc < HID / FZ_KC; ++kc) {
+            const int buf = kc & 1;
+            if (kc + 1 < HID / FZ_KC) {
+                load_chunk(buf ^ 1, kc + 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const bf16 *wb = sW + buf * FZ_KC * FZ_LDH;
+#pragma unroll
+            for (int ks = 0; ks < FZ_KC; ks += 16) {
+                uint32_t af[2][4], bfr[4][4];
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+                    ldsm_x4(af[i], sH + (wm * 32 + i * 16 + (lane & 15)) * FZ_LDH + kc * FZ_KC + ks +
+                                       (lane >> 4) * 8);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    ldsm_x4_t(bfr[jj], wb + (ks + r8 + (j8 & 1) * 8) * FZ_LDH + wn * 64 + jj * 16 +
+                                           (j8 >> 1) * 8);
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        mma_bf16(acc[i][j], af[i], bfr[j >> 1][(j & 1) * 2], bfr[j >> 1][(j & 1) * 2 + 1]);
+            }
+            __syncthreads();  // chunk buffer and tile reads done before they are overwritten
+        }
+        // epilogue: bias + SiLU, BF16 result replaces the tile
+        const float *bias = p + off_b(l);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int r = wm * 32 + i * 16 + g + h * 8;
+                    const int nn = wn * 64 + j * 8 + 2 * q;
+                    const float z0 = acc[i][j][2 * h] + bias[nn], z1 = acc[i][j][2 * h + 1] + bias[nn + 1];
+                    *reinterpret_cast<__nv_bfloat162 *>(sH + r * FZ_LDH + nn) =
+                        __floats2bfloat162_rn(silu(z0), silu(z1));
+                }
+    }
+    __syncthreads();
+    // layer 5: one (row, output) dot product per thread
+    {
+        const int r = tid >> 2, o = tid & 3;
+        const int64_t gr = row0 + r;
+        float v = p[OFF_B5 + o];
+        for (int nn = 0; nn < HID; ++nn)
+            v += __bfloat162float(sH[r * FZ_LDH + nn]) * bfv(pb, OFF_W5 + nn * NOUT + o);
+        if (gr < n_rows) y[gr * NOUT + o] = v;
+    }
+}
+
 template <bool A_T, bool B_T, int EPI>
 void gemm(const bf16 *A, const bf16 *B, int M, int N, int K, int lda, int ldb, int splits,
           EpiArgs ep, cudaStream_t st)
@@ -529,6 +638,11 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
     }
     cudaMemset(m->m1, 0, NPARAM * sizeof(float));
     cudaMemset(m->m2, 0, NPARAM * sizeof(float));
+    if (cudaFuncSetAttribute(mlp_fused_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FZ_SMEM) != cudaSuccess) {
+        free_mlp(m);
+        return ODX_ERR_CUDA;
+    }
     init_params<<<blocks_for(NPARAM, 256), 256>>>(m->p, m->pb, seed);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         free_mlp(m);
@@ -573,12 +687,9 @@ int32_t odx_mlp_forward(odx_mlp *m, const float *x, int64_t n, float *y, void *s
     for (int64_t b0 = 0; b0 < n; b0 += m->max_batch) {
         const int64_t nb = std::min<int64_t>(m->max_batch, n - b0);
         const int64_t B = round128(nb);
-        MLP_CUDA(cudaMemsetAsync(m->xin, 0, B * NIN * sizeof(float), st));
-        MLP_CUDA(cudaMemcpyAsync(m->xin, x + b0 * NIN, nb * NIN * sizeof(float),
-                                 cudaMemcpyDeviceToDevice, st));
-        forward(m, m->xin, B, nb, m->Y, nullptr, false, st);
-        MLP_CUDA(cudaMemcpyAsync(y + b0 * NOUT, m->Y, nb * NOUT * sizeof(float),
-                                 cudaMemcpyDeviceToDevice, st));
+        (void)B;
+        mlp_fused_forward<<<blocks_for(nb, FZ_ROWS), FZ_THREADS, FZ_SMEM, st>>>(
+            x + b0 * NIN, m->pb, m->p, nb, y + b0 * NOUT);
     }
     MLP_CUDA(cudaGetLastError());
     return ODX_OK;
@@ -667,10 +778,8 @@ int32_t odx_surrogate_render(odx_mlp *m, const odx_scene *scene, double band, do
     bcrit_table<<<blocks_for(BCRIT_N, 128), 128, 0, st>>>(scene->a, scene->theta_obs, scene->r_in,
                                                           m->bcrit);
     surrogate_inputs<<<blocks_for(n_pad, 256), 256, 0, st>>>(m->scene_tab, n_pad, m->surr_x);
-    for (int64_t b0 = 0; b0 < n_pad; b0 += m->max_batch) {
-        const int64_t B = std::min<int64_t>(m->max_batch, n_pad - b0);
-        forward(m, m->surr_x + b0 * NIN, B, B, m->surr_y + b0 * NOUT, nullptr, false, st);
-    }
+    mlp_fused_forward<<<blocks_for(n_pad, FZ_ROWS), FZ_THREADS, FZ_SMEM, st>>>(
+        m->surr_x, m->pb, m->p, n_pad, m->surr_y);
     surrogate_classify<<<blocks_for(n, 256), 256, 0, st>>>(m->scene_tab, m->surr_y, m->bcrit, band,
                                                           (float)p_lo, (float)p_hi, image,
                                                           m->fb_rays, m->fb_pix, m->fb_count);
