@@ -293,16 +293,22 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
     d.ray_begin = ray_begin;
     d.n_rays = n_rays;
     d.img_offset = img_offset;
-    d.f_ne_index = (float)s.ne_index;
-    d.f_inv_2w2 = s.theta_width > 0.0 ? (float)(1.0 / (2.0 * s.theta_width * s.theta_width)) : 0.f;
-    d.f_T0 = (float)s.T0;
-    d.f_inv_T0 = s.T0 > 0.0 ? (float)(1.0 / s.T0) : 0.f;
-    d.f_T_index = (float)s.T_index;
-    d.f_C_norm = (float)s.C_norm;
     d.f_r_out = (float)s.r_out;
     d.f_hmax_frac = (float)s.hmax_frac;
     d.f_rtol32 = (float)s.rtol_fp32;
-    for (int k = 0; k < ODX_MAX_FREQ; ++k) d.f_freqs[k] = (float)s.freqs[k];
+    // torus (Section 4.2): n_e^2 = r^(-2 ne_index) exp(-cos^2 / w^2), T_e = T0 r^-T_index
+    const bool torus = s.emitter == ODX_EMIT_TORUS && s.T0 > 0.0 && s.theta_width > 0.0;
+    d.f_T_index = (float)s.T_index;
+    d.f_inv_T0 = torus ? (float)(1.0 / s.T0) : 0.f;
+    d.f_lr_pref = (float)(0.5 * s.T_index - 2.0 * s.ne_index);
+    d.f_c2_pref = torus ? (float)(-1.0 / (s.theta_width * s.theta_width)) : 0.f;
+    d.f_pref0 = torus ? (float)(s.C_norm / sqrt(s.T0)) : 0.f;
+    const int nf = (s.n_freq > 0 && s.n_freq <= ODX_MAX_FREQ) ? s.n_freq : 0;
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) {
+        const double nu = nf > 0 ? s.freqs[k < nf ? k : nf - 1] : 1.0;
+        d.f_nu[k] = (float)nu;
+        d.f_inv_nu3[k] = (nu > 0.0) ? (float)(1.0 / (nu * nu * nu)) : 0.f;
+    }
 }
 
 // Argument checks of odx_render for callers without a context (no message is stored).

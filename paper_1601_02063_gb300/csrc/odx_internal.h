@@ -17,10 +17,15 @@ struct DevScene {
     int64_t n_rays;     // n_alpha * n_beta (list mode: n)
     int64_t img_offset; // offset of this scene's image planes, in doubles
     int64_t pad;
-    // FP32 copies of the parameters the FP32 stages read (filled by fill_dev_scene)
-    float f_ne_index, f_inv_2w2, f_T0, f_T_index, f_C_norm, f_r_out, f_hmax_frac, f_rtol32;
-    float f_inv_T0, f_pad[3];
-    float f_freqs[ODX_MAX_FREQ];
+    // FP32 constants of the FP32 stages (filled by fill_dev_scene)
+    float f_r_out, f_hmax_frac, f_rtol32;
+    float f_T_index;   // 1/T_e = exp(T_index ln r) / T0
+    float f_inv_T0;
+    float f_lr_pref;   // C n_e^2 T_e^-1/2 = f_pref0 exp(f_lr_pref ln r + f_c2_pref cos^2 theta)
+    float f_c2_pref;
+    float f_pref0;
+    float f_nu[ODX_MAX_FREQ];       // observed frequencies, padded past n_freq with the last
+    float f_inv_nu3[ODX_MAX_FREQ];  // 1 / f_nu^3
 };
 
 // One scene-table entry for a scene whose rays start at ray_begin (all table builders).

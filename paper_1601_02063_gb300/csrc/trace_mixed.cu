@@ -111,10 +111,8 @@ __global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
 template <int NF>
 struct RayM {
     float yh[6], yl[6];  // state pairs: r, theta, phi, t, p_r, p_theta
-    float k1f[6];        // FP32 first stage (valid when mode == 0)
     float th[NF + 1], tl[NF + 1];
     float Ih[NF + 1], Il[NF + 1];
-    float kt1f[NF + 1], kI1f[NF + 1];
     float hf, hsf;       // FP32 step and error-scale step
     double hd, hsd;      // FP64 step and error-scale step
     float Lh, Ll, af, sgnf, r_switch, r_stopf, r_startf, r_inf;
@@ -234,20 +232,108 @@ __device__ __noinline__ void locate_crossing64m(const Geo<double> &g, const doub
     for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
 }
 
-__device__ __forceinline__ MediumT<float> medium32(const DevScene &S, float r_isco)
+// FP32 torus constants of one lane's scene (Section 4.2, Eqs. 30-31), folded so that a stage
+// needs one logarithm and two exponentials besides the two per frequency.
+template <int NF>
+struct MediumF {
+    float r_isco, T_index, inv_T0, lr_pref, c2_pref, pref0;
+    float nu[NF + 1], inv_nu3[NF + 1];
+};
+
+template <int NF>
+__device__ __forceinline__ MediumF<NF> medium_f(const DevScene &S, float r_isco)
 {
-    MediumT<float> m;
-    m.ne_index = S.f_ne_index;
-    m.inv_2w2 = S.f_inv_2w2;
-    m.T0 = S.f_T0;
-    m.inv_T0 = S.f_inv_T0;
-    m.T_index = S.f_T_index;
-    m.C_norm = S.f_C_norm;
+    MediumF<NF> m;
     m.r_isco = r_isco;
-    m.n_freq = S.s.n_freq;
+    m.T_index = S.f_T_index;
+    m.inv_T0 = S.f_inv_T0;
+    m.lr_pref = S.f_lr_pref;
+    m.c2_pref = S.f_c2_pref;
+    m.pref0 = S.f_pref0;
 #pragma unroll
-    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = S.f_freqs[k];
+    for (int k = 0; k < NF + 1; ++k) {
+        m.nu[k] = S.f_nu[k < ODX_MAX_FREQ ? k : 0];
+        m.inv_nu3[k] = S.f_inv_nu3[k < ODX_MAX_FREQ ? k : 0];
+    }
     return m;
+}
+
+// Hardware reciprocal (relative error ~1 ulp; the FP32 stages run at rtol ~1e-6).
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
+
+// FP32 right-hand side of one stage: geodesic (Eqs. 4, 5, 9, 12, 14, 15, with the
+// super-Hamiltonian terms F of the FP64 form) and, for NF > 0, the torus transfer terms
+// (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
+// Frequency slots past the scene's n_freq repeat its last frequency (never written out).
+template <int NF>
+__device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> &m,
+                                         const float *in, float f[6], float *ft, float *fI)
+{
+    const float r = in[0], pr = in[2], pth = in[3];
+    float s, c;
+    __sincosf(in[1], &s, &c);  // |x| <= pi up to pole passages: abs. error <= 2^-21.4
+    s = fmaxf(s, 1e-8f);
+    const float a = g.a, L = g.L;
+    const float r2 = r * r, a2 = a * a, s2 = s * s;
+    const float Sig = r2 + a2 * c * c;
+    const float Del = r2 - 2.f * r + a2;
+    const float iSD = rcp_fast(Sig * Del);
+    const float iS = Del * iSD;
+    const float iD = Sig * iSD;
+    const float is = rcp_fast(s);
+    const float is2 = is * is;
+    const float rr = r2 + a2;
+    const float P = rr - a * L;
+    const float q = L * is - a * s;
+    const float pr2 = pr * pr, pth2 = pth * pth;
+    const float F = Del * pr2 + pth2 + q * q - P * P * iD;
+    const float kap = pth2 + L * L * is2 + a2 * s2;
+    const float rm1 = r - 1.f;
+    const float twor = 2.f * r;
+    f[0] = g.sgn * (Del * pr * iS);
+    f[1] = g.sgn * (pth * iS);
+    f[2] = g.sgn * ((twor * a + (Sig - twor) * L * is2) * iSD);
+    f[3] = g.sgn * (1.f + (twor * rr - twor * a * L) * iSD);
+    f[4] = g.sgn * ((-kap * rm1 + twor * rr - 2.f * a * L) * iSD - 2.f * pr2 * rm1 * iS +
+                    F * (rm1 * iSD + r * iS * iS));
+    f[5] = g.sgn * (s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS);
+    if constexpr (NF > 0) {
+        // Keplerian flow where r >= r_ISCO and timelike, else ZAMO; 1/g = u^t (1 - Omega L)
+        const float A = rr * rr - a2 * Del * s2;
+        const float gtt = -(1.f - twor * iS);
+        const float gtp = -twor * a * s2 * iS;
+        const float gpp = A * s2 * iS;
+        float Om = rcp_fast(r * r * rsqrtf(r) + a);
+        float N = gtt + 2.f * gtp * Om + gpp * Om * Om;
+        if (!(r >= m.r_isco && N < 0.f)) {
+            Om = twor * a * rcp_fast(A);
+            N = gtt + 2.f * gtp * Om + gpp * Om * Om;
+        }
+        const float ig = (1.f - Om * L) * rsqrtf(-N);
+        const float gg = rcp_fast(ig);
+        const float lr = __logf(r);
+        // C n_e^2 T_e^-1/2 g^2, and nu0 / T_e per unit observed frequency
+        const float Q = m.pref0 * __expf(m.lr_pref * lr + m.c2_pref * c * c) * gg * gg;
+        const float xi = ig * m.inv_T0 * __expf(m.T_index * lr);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            const float x = m.nu[k] * xi;
+            const float w = Q * m.inv_nu3[k];  // C n_e^2 T_e^-1/2 / (g nu0^3)
+            ft[k] = 0.5f * w * one_minus_exp(x, __expf(-x));  // Eq. 30
+            fI[k] = w * __expf(-(x + in[4 + k]));             // Eq. 31
+        }
+    }
+}
+
+// Sign of cos(theta) for theta = hi + lo: the hardware cosine away from the zeros, the
+// accurate one corrected by the low word near them.
+__device__ __forceinline__ bool cos_positive(float hi, float lo)
+{
+    const float c = __cosf(hi);
+    if (fabsf(c) > 1e-3f) return c > 0.f;
+    float sn, cs;
+    sincosf(hi, &sn, &cs);
+    return cs - lo * sn > 0.f;
 }
 
 // Record the crossing; returns true when the ray stops on the thin disk (the crossing state
@@ -275,27 +361,126 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, cons
 }
 
 // One FP32 Cash-Karp attempt.  Returns the new status.
+//
+// The six stages run as a loop around one inlined right-hand side (one copy of its code in
+// the instruction cache, no call).  Each stage's derivative is folded at once into the
+// inputs of the later stages (acc[j]: the weighted sum for stage j + 1), the fifth-order
+// sum and the error estimate, so no stage derivative is kept; t and phi, which no
+// right-hand side reads, enter only those two sums.  The first stage is evaluated afresh
+// at every attempt (a rejected attempt repeats it exactly).
 template <int NF>
-__device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R,
-                                          const MediumT<float> &mf)
+__device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const MediumF<NF> &mf)
 {
+    constexpr int NG = 4 + NF;  // stage inputs: r, theta, p_r, p_theta, tau_k
     const Geo<float> g{R.af, R.Lh, R.sgnf};
-    if (R.mode != 0) {  // (re)enter FP32: first stage in FP32
-        derivs_stage<float, NF>(g, mf, R.yh, R.th, R.k1f, R.kt1f, R.kI1f);
+    if (R.mode != 0) {  // (re)enter FP32
         if (R.mode == 1) R.hf = (float)R.hd;
         R.hsf = R.hf;
         R.mode = 0;
     }
     const float h = R.hf;
-    float dy[6], e[6], dtau[NF + 1], dI[NF + 1];
-    ck_attempt<float, NF>(g, mf, R.yh, R.k1f, R.th, R.kt1f, R.kI1f, h, dy, e, dtau, dI);
+    float y0[NG];
+    y0[0] = R.yh[0];
+    y0[1] = R.yh[1];
+    y0[2] = R.yh[4];
+    y0[3] = R.yh[5];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) y0[4 + k] = R.th[k];
+    float in[NG];
+#pragma unroll
+    for (int c = 0; c < NG; ++c) in[c] = y0[c];
+    float acc[5][NG], k1[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
+
+#define ODX_ACC(J, COEF)                                                   \
+    _Pragma("unroll") for (int c = 0; c < NG; ++c) acc[J][c] = fmaf((float)(COEF), kf[c], acc[J][c]);
+#define ODX_NEXT(J)                                                        \
+    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(h, acc[J][c], y0[c]);
+#define ODX_SUMS(B, E)                                                     \
+    _Pragma("unroll") for (int i = 0; i < 6; ++i) {                        \
+        dy[i] = fmaf((float)(B), f[i], dy[i]);                             \
+        e[i] = fmaf((float)(E), f[i], e[i]);                               \
+    }                                                                      \
+    _Pragma("unroll") for (int k = 0; k < NF; ++k) {                       \
+        dtau[k] = fmaf((float)(B), ft[k], dtau[k]);                        \
+        dI[k] = fmaf((float)(B), fI[k], dI[k]);                            \
+    }
+
+#pragma unroll 1
+    for (int st = 0; st < 6; ++st) {
+        float f[6], ft[NF + 1], fI[NF + 1];
+        derivs32<NF>(g, mf, in, f, ft, fI);
+        float kf[NG];
+        kf[0] = f[0];
+        kf[1] = f[1];
+        kf[2] = f[4];
+        kf[3] = f[5];
+#pragma unroll
+        for (int k = 0; k < NF; ++k) kf[4 + k] = ft[k];
+        switch (st) {
+        case 0:
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                acc[0][c] = (float)CK_A21 * kf[c];
+                acc[1][c] = (float)CK_A31 * kf[c];
+                acc[2][c] = (float)CK_A41 * kf[c];
+                acc[3][c] = (float)CK_A51 * kf[c];
+                acc[4][c] = (float)CK_A61 * kf[c];
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                k1[i] = f[i];
+                dy[i] = (float)CK_B1 * f[i];
+                e[i] = (float)CK_E1 * f[i];
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                dtau[k] = (float)CK_B1 * ft[k];
+                dI[k] = (float)CK_B1 * fI[k];
+            }
+            ODX_NEXT(0)
+            break;
+        case 1:  // b2 = e2 = 0
+            ODX_ACC(1, CK_A32)
+            ODX_ACC(2, CK_A42)
+            ODX_ACC(3, CK_A52)
+            ODX_ACC(4, CK_A62)
+            ODX_NEXT(1)
+            break;
+        case 2:
+            ODX_ACC(2, CK_A43)
+            ODX_ACC(3, CK_A53)
+            ODX_ACC(4, CK_A63)
+            ODX_SUMS(CK_B3, CK_E3)
+            ODX_NEXT(2)
+            break;
+        case 3:
+            ODX_ACC(3, CK_A54)
+            ODX_ACC(4, CK_A64)
+            ODX_SUMS(CK_B4, CK_E4)
+            ODX_NEXT(3)
+            break;
+        case 4:  // b5 = 0
+            ODX_ACC(4, CK_A65)
+#pragma unroll
+            for (int i = 0; i < 6; ++i) e[i] = fmaf((float)CK_E5, f[i], e[i]);
+            ODX_NEXT(4)
+            break;
+        default:
+            ODX_SUMS(CK_B6, CK_E6)
+            break;
+        }
+    }
+#undef ODX_ACC
+#undef ODX_NEXT
+#undef ODX_SUMS
+
     float errmax = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * R.k1f[i]) + 1e-30f;
-        errmax = fmaxf(errmax, fabsf(e[i] / sc));
+        const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * k1[i]) + 1e-30f;
+        errmax = fmaxf(errmax, __fdividef(fabsf(h * e[i]), sc));
     }
-    errmax /= S.f_rtol32;
+    errmax = __fdividef(errmax, S.f_rtol32);
     if (isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.f)) {
         ++R.n_rej;
@@ -304,21 +489,27 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R,
     }
     ++R.n_acc;
     const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
-    if ((cosf(R.yh[1]) > 0.f) != (cosf(R.yh[1] + dy[1]) > 0.f)) {
-        float ch[6], cl[6];
-        locate_crossing32(g, R.yh, R.yl, R.k1f, h, ch, cl);
-        if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dy[i] *= h;
+    {
+        float nh = R.yh[1], nl = R.yl[1];
+        df_add(nh, nl, dy[1]);
+        if (cos_positive(R.yh[1], R.yl[1]) != cos_positive(nh, nl)) {
+            float ch[6], cl[6];
+            locate_crossing32(g, R.yh, R.yl, k1, h, ch, cl);
+            if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
+        }
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) df_add(R.yh[i], R.yl[i], dy[i]);
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        df_add(R.th[k], R.tl[k], dtau[k]);
-        df_add(R.Ih[k], R.Il[k], dI[k]);
+        df_add(R.th[k], R.tl[k], h * dtau[k]);
+        df_add(R.Ih[k], R.Il[k], h * dI[k]);
     }
     if (R.yh[0] < R.r_stopf) return ODX_CAPTURED;
-    derivs_stage<float, NF>(g, mf, R.yh, R.th, R.k1f, R.kt1f, R.kI1f);
-    if (R.k1f[0] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
+    // escape: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
+    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
     R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
     R.hsf = R.hf;
     return ODX_RUNNING;
@@ -411,7 +602,7 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
 {
     const int lane = threadIdx.x & 31;
     RayM<NF> R;
-    MediumT<float> mf{};
+    MediumF<NF> mf{};
     bool live = false;
     WarpQueue q;
     q.init(A);
@@ -448,7 +639,7 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
             R.hf = m.h0;
             R.hsf = m.h0;
             R.mode = -1;
-            if constexpr (NF > 0) mf = medium32(S, m.r_isco);
+            mf = medium_f<NF>(S, m.r_isco);
             live = true;
         }
         const unsigned act = __ballot_sync(kFull, live);
