@@ -29,7 +29,8 @@ struct MixedInit {  // init pass -> tracer
     float yh[5], yl[5];  // r, theta, phi, p_r, p_theta (t starts at 0)
     float Lh, Ll;        // angular momentum
     float r_stop, r_in, r_isco, a;
-    float h0, r_switch, pad0, pad1;
+    float h0, r_switch;
+    float Ch, Cl;        // a^2 - a L (a the FP32 spin) as a pair, for the near-horizon stages
 };
 struct MixedOut {  // tracer -> finish pass
     int32_t status, n_acc, n_rej, n_cross;
@@ -103,53 +104,73 @@ __global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
     m.a = (float)a;
     m.h0 = (float)fmin(S.s.h0, S.s.hmax_frac * io.y[0]);
     m.r_switch = (float)S.s.r_switch;
-    m.pad0 = m.pad1 = 0.f;
+    {
+        const double af = (double)m.a, Ld = (double)m.Lh + (double)m.Ll;
+        df_set(m.Ch, m.Cl, af * af - af * Ld);
+    }
     store80(A.records + id, m);
 }
 
 // ---- pass 2: FP32 tracer ------------------------------------------------------------------
+constexpr int kMixedBlock = 128;  // threads per block of the tracing kernel (at most)
+
+// Per-lane state that the FP32 stages read: registers.
 template <int NF>
 struct RayM {
-    float yh[6], yl[6];  // state pairs: r, theta, phi, t, p_r, p_theta
-    float th[NF + 1], tl[NF + 1];
-    float Ih[NF + 1], Il[NF + 1];
-    float hf, hsf;       // FP32 step and error-scale step
-    double hd, hsd;      // FP64 step and error-scale step
-    float Lh, Ll, af, sgnf, r_switch, r_stopf, r_startf, r_inf;
-    float rch, rcl, pch, pcl;  // first crossing pairs
-    int64_t id;
-    int32_t scene, mode, n_acc, n_rej, n_cross, n64;
+    float yh[6];       // state high words: r, theta, phi, t, p_r, p_theta
+    float th[NF + 1];  // tau high words
+    float hf, hsf;     // FP32 step and error-scale step
+    float Lh, af, sgnf, r_switch;
+    int32_t scene, mode, n_acc, n_rej;
+};
+
+// Per-lane state touched once per accepted step or less: shared memory, laid out
+// [field][thread] (consecutive lanes in consecutive banks), which leaves the registers to
+// the stage loop.
+template <int NF>
+struct ColdM {
+    float yl[6][kMixedBlock];  // state low words
+    float tl[NF + 1][kMixedBlock];
+    float Ih[NF + 1][kMixedBlock], Il[NF + 1][kMixedBlock];
+    double hd[kMixedBlock], hsd[kMixedBlock];  // FP64 step and error-scale step
+    float Ll[kMixedBlock], r_stop[kMixedBlock], r_start[kMixedBlock], r_in[kMixedBlock];
+    float rch[kMixedBlock], rcl[kMixedBlock], pch[kMixedBlock], pcl[kMixedBlock];
+    float Ch[kMixedBlock], Cl[kMixedBlock];  // a^2 - a L as a pair
+    long long id[kMixedBlock];
+    int32_t n_cross[kMixedBlock], n64[kMixedBlock];
 };
 
 template <int NF>
 __device__ __forceinline__ void write_slot(const TraceArgs &A, const DevScene &S,
-                                           const RayM<NF> &R, int32_t status)
+                                           const RayM<NF> &R, const ColdM<NF> &C, int32_t status)
 {
+    const int t = threadIdx.x;
+    const long long id = C.id[t];
     MixedOut o;
     o.status = status;
     o.n_acc = R.n_acc;
     o.n_rej = R.n_rej;
-    o.n_cross = R.n_cross;
-    o.rch = R.rch;
-    o.rcl = R.rcl;
-    o.pch = R.pch;
-    o.pcl = R.pcl;
+    o.n_cross = C.n_cross[t];
+    o.rch = C.rch[t];
+    o.rcl = C.rcl[t];
+    o.pch = C.pch[t];
+    o.pcl = C.pcl[t];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         o.yh[i] = R.yh[state_index(i)];
-        o.yl[i] = R.yl[state_index(i)];
+        o.yl[i] = C.yl[state_index(i)][t];
     }
-    o.n64 = R.n64;
+    o.n64 = C.n64[t];
     o.pad = 0;
-    store80(A.records + R.id, o);
+    store80(A.records + id, o);
     if constexpr (NF > 0) {
         if (A.image) {
-            double *img = A.image + S.img_offset + (R.id - S.ray_begin);
+            double *img = A.image + S.img_offset + (id - S.ray_begin);
 #pragma unroll
             for (int k = 0; k < NF; ++k)  // packed invariant-intensity pair, finished in pass 3
                 if (k < S.s.n_freq)
                     *reinterpret_cast<float2 *>(img + (int64_t)k * S.n_rays) =
-                        make_float2(R.Ih[k], R.Il[k]);
+                        make_float2(C.Ih[k][t], C.Il[k][t]);
         }
     }
 }
@@ -265,18 +286,90 @@ __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); 
 // super-Hamiltonian terms F of the FP64 form) and, for NF > 0, the torus transfer terms
 // (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
 // Frequency slots past the scene's n_freq repeat its last frequency (never written out).
+// Low word of s = fl(x + y) (Knuth two-sum).
+__device__ __forceinline__ float two_sum_err(float x, float y, float s)
+{
+    const float bp = s - x;
+    return (x - (s - bp)) + (y - bp);
+}
+
+// Where the low words of the stage inputs r, p_r come from, for the near-horizon stages:
+// r = y0r + tr (rounded) with the state's low word ylr; p_r likewise.
+struct PairStage {
+    float y0r, tr, ylr, y0t, tt, ylt, y0p, tp, ylp, Ch, Cl;
+};
+
+// sin and cos of theta = hi + lo near a pole (|sin theta| < 1/4).  There the FP32 stage
+// input theta near pi carries an absolute rounding error of up to 1.2e-7, a large relative
+// error in sin(theta) and in the L^2 / sin^4(theta) terms.  theta is reduced by the nearest
+// multiple k pi in pair arithmetic (pi = kPiHi + kPiLo) and the reduced angle d, |d| < 0.26,
+// goes through the Taylor series of sin and cos (truncation below 2e-11).
+constexpr float kPiHi = 3.14159274101257324f, kPiLo = -8.74227766e-8f;
+__device__ __forceinline__ void sincos_pole(float hi, float lo, float &s, float &c)
+{
+    const float k = rintf(hi * 0.318309886f);
+    const float d = fmaf(-k, kPiHi, hi) + fmaf(-k, kPiLo, lo);
+    const float d2 = d * d;
+    float sd = d * (1.f - d2 * (1.f / 6.f) * (1.f - d2 * (1.f / 20.f) * (1.f - d2 * (1.f / 42.f))));
+    float cd = 1.f - d2 * 0.5f * (1.f - d2 * (1.f / 12.f) * (1.f - d2 * (1.f / 30.f) *
+                                                          (1.f - d2 * (1.f / 56.f))));
+    if (((int)k) & 1) {
+        sd = -sd;
+        cd = -cd;
+    }
+    s = sd;
+    c = cd;
+}
+
+// Near the horizon (Delta < r^2 / 4) F = 2 Sigma H is the difference of two terms of size
+// P^2 / Delta that cancel to the size of the constraint violation, and Delta itself loses
+// its leading digits.  With FP32 stage inputs the rounding of r alone makes F, and through
+// it dp_theta/ds, noise of order one there, which stalls the step control of rays with small
+// p_theta.  In that region Delta, Delta p_r - P and so F are formed in float-pair arithmetic
+// from the stage inputs' low words.
+__device__ __forceinline__ void near_horizon(float r, float pr, float a, const PairStage &ps,
+                                             float &Del, float &D, float &S)
+{
+    const float rl = two_sum_err(ps.y0r, ps.tr, r) + ps.ylr;
+    const float pl = two_sum_err(ps.y0p, ps.tp, pr) + ps.ylp;
+    const float q2 = __fmul_rn(r, r);  // r^2 = q2 + q2e (products kept out of contractions)
+    const float q2e = fmaf(2.f * r, rl, fmaf(r, r, -q2));
+    const float a2h = __fmul_rn(a, a), a2l = fmaf(a, a, -a2h);
+    // Delta = r^2 - 2 r + a^2 (q2 - 2 r is exact for 1 <= r <= 4, Sterbenz)
+    const float d1 = q2 - 2.f * r;
+    float Dh = d1 + a2h;
+    float Dl = two_sum_err(d1, a2h, Dh) + q2e - 2.f * rl + a2l;
+    const float t = Dh + Dl;
+    Dl = Dl - (t - Dh);
+    Dh = t;
+    // u = Delta p_r, P = r^2 + (a^2 - a L), D = u - P
+    const float uh = __fmul_rn(Dh, pr);
+    const float ul = fmaf(Dl, pr, fmaf(Dh, pl, fmaf(Dh, pr, -uh)));
+    const float Ph = q2 + ps.Ch;
+    const float Pl = two_sum_err(q2, ps.Ch, Ph) + q2e + ps.Cl;
+    const float dh = uh - Ph;
+    D = dh + (two_sum_err(uh, -Ph, dh) + (ul - Pl));
+    S = uh + Ph;
+    Del = Dh;
+}
+
 template <int NF>
 __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> &m,
-                                         const float *in, float f[6], float *ft, float *fI)
+                                         const float *in, const PairStage &ps, float f[6],
+                                         float *ft, float *fI)
 {
     const float r = in[0], pr = in[2], pth = in[3];
     float s, c;
     __sincosf(in[1], &s, &c);  // |x| <= pi up to pole passages: abs. error <= 2^-21.4
+    if (fabsf(s) < 0.25f) sincos_pole(in[1], two_sum_err(ps.y0t, ps.tt, in[1]) + ps.ylt, s, c);
     s = fmaxf(s, 1e-8f);
     const float a = g.a, L = g.L;
     const float r2 = r * r, a2 = a * a, s2 = s * s;
     const float Sig = r2 + a2 * c * c;
-    const float Del = r2 - 2.f * r + a2;
+    float Del = r2 - 2.f * r + a2;
+    const bool nh = Del < 0.25f * r2;
+    float Dm = 0.f, Sm = 0.f;  // Delta p_r -+ P (near the horizon)
+    if (nh) near_horizon(r, pr, a, ps, Del, Dm, Sm);
     const float iSD = rcp_fast(Sig * Del);
     const float iS = Del * iSD;
     const float iD = Sig * iSD;
@@ -286,7 +379,7 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> 
     const float P = rr - a * L;
     const float q = L * is - a * s;
     const float pr2 = pr * pr, pth2 = pth * pth;
-    const float F = Del * pr2 + pth2 + q * q - P * P * iD;
+    const float F = nh ? fmaf(Dm * Sm, iD, pth2 + q * q) : Del * pr2 + pth2 + q * q - P * P * iD;
     const float kap = pth2 + L * L * is2 + a2 * s2;
     const float rm1 = r - 1.f;
     const float twor = 2.f * r;
@@ -305,9 +398,10 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> 
         const float gpp = A * s2 * iS;
         float Om = rcp_fast(r * r * rsqrtf(r) + a);
         float N = gtt + 2.f * gtp * Om + gpp * Om * Om;
-        if (!(r >= m.r_isco && N < 0.f)) {
-            Om = twor * a * rcp_fast(A);
-            N = gtt + 2.f * gtp * Om + gpp * Om * Om;
+        if (!(r >= m.r_isco && N < 0.f)) {  // ZAMO: g_tt - g_tphi^2 / g_phiphi = -Sigma Delta / A
+            const float iA = rcp_fast(A);
+            Om = twor * a * iA;
+            N = -Sig * Del * iA;
         }
         const float ig = (1.f - Om * L) * rsqrtf(-N);
         const float gg = rcp_fast(ig);
@@ -339,21 +433,22 @@ __device__ __forceinline__ bool cos_positive(float hi, float lo)
 // Record the crossing; returns true when the ray stops on the thin disk (the crossing state
 // becomes the final state).
 template <int NF>
-__device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, const float ch[6],
-                                            const float cl[6])
+__device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, ColdM<NF> &C,
+                                            const float ch[6], const float cl[6])
 {
-    ++R.n_cross;
-    if (R.n_cross == 1) {
-        R.rch = ch[0];
-        R.rcl = cl[0];
-        R.pch = ch[2];
-        R.pcl = cl[2];
+    const int t = threadIdx.x;
+    const int n = ++C.n_cross[t];
+    if (n == 1) {
+        C.rch[t] = ch[0];
+        C.rcl[t] = cl[0];
+        C.pch[t] = ch[2];
+        C.pcl[t] = cl[2];
     }
-    if (S.s.emitter == ODX_EMIT_THIN_DISK && ch[0] >= R.r_inf && ch[0] <= S.f_r_out) {
+    if (S.s.emitter == ODX_EMIT_THIN_DISK && ch[0] >= C.r_in[t] && ch[0] <= S.f_r_out) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             R.yh[i] = ch[i];
-            R.yl[i] = cl[i];
+            C.yl[i][t] = cl[i];
         }
         return true;
     }
@@ -369,12 +464,14 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, cons
 // right-hand side reads, enter only those two sums.  The first stage is evaluated afresh
 // at every attempt (a rejected attempt repeats it exactly).
 template <int NF>
-__device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const MediumF<NF> &mf)
+__device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<NF> &C,
+                                          const MediumF<NF> &mf)
 {
+    const int t = threadIdx.x;
     constexpr int NG = 4 + NF;  // stage inputs: r, theta, p_r, p_theta, tau_k
     const Geo<float> g{R.af, R.Lh, R.sgnf};
     if (R.mode != 0) {  // (re)enter FP32
-        if (R.mode == 1) R.hf = (float)R.hd;
+        if (R.mode == 1) R.hf = (float)C.hd[t];
         R.hsf = R.hf;
         R.mode = 0;
     }
@@ -389,12 +486,20 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const 
     float in[NG];
 #pragma unroll
     for (int c = 0; c < NG; ++c) in[c] = y0[c];
+    PairStage ps{y0[0], 0.f, C.yl[0][t], y0[1], 0.f, C.yl[1][t], y0[2], 0.f, C.yl[4][t],
+                 C.Ch[t], C.Cl[t]};
     float acc[5][NG], k1[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
 
 #define ODX_ACC(J, COEF)                                                   \
     _Pragma("unroll") for (int c = 0; c < NG; ++c) acc[J][c] = fmaf((float)(COEF), kf[c], acc[J][c]);
 #define ODX_NEXT(J)                                                        \
-    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(h, acc[J][c], y0[c]);
+    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(h, acc[J][c], y0[c]); \
+    ps.tr = __fmul_rn(h, acc[J][0]);                                       \
+    ps.tt = __fmul_rn(h, acc[J][1]);                                       \
+    ps.tp = __fmul_rn(h, acc[J][2]);                                       \
+    in[0] = __fadd_rn(y0[0], ps.tr);                                       \
+    in[1] = __fadd_rn(y0[1], ps.tt);                                       \
+    in[2] = __fadd_rn(y0[2], ps.tp);
 #define ODX_SUMS(B, E)                                                     \
     _Pragma("unroll") for (int i = 0; i < 6; ++i) {                        \
         dy[i] = fmaf((float)(B), f[i], dy[i]);                             \
@@ -408,7 +513,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const 
 #pragma unroll 1
     for (int st = 0; st < 6; ++st) {
         float f[6], ft[NF + 1], fI[NF + 1];
-        derivs32<NF>(g, mf, in, f, ft, fI);
+        derivs32<NF>(g, mf, in, ps, f, ft, fI);
         float kf[NG];
         kf[0] = f[0];
         kf[1] = f[1];
@@ -490,26 +595,37 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const 
     ++R.n_acc;
     const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dy[i] *= h;
+    for (int i = 0; i < 6; ++i) dy[i] = __fmul_rn(dy[i], h);  // rounded before the two-sums
     {
-        float nh = R.yh[1], nl = R.yl[1];
+        float nh = R.yh[1], nl = C.yl[1][t];
+        const bool c0 = cos_positive(nh, nl);
         df_add(nh, nl, dy[1]);
-        if (cos_positive(R.yh[1], R.yl[1]) != cos_positive(nh, nl)) {
-            float ch[6], cl[6];
-            locate_crossing32(g, R.yh, R.yl, k1, h, ch, cl);
-            if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
+        if (c0 != cos_positive(nh, nl)) {
+            float yl[6], ch[6], cl[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) yl[i] = C.yl[i][t];
+            locate_crossing32(g, R.yh, yl, k1, h, ch, cl);
+            if (on_crossing<NF>(S, R, C, ch, cl)) return ODX_DISK_HIT;
         }
     }
 #pragma unroll
-    for (int i = 0; i < 6; ++i) df_add(R.yh[i], R.yl[i], dy[i]);
+    for (int i = 0; i < 6; ++i) {
+        float lo = C.yl[i][t];
+        df_add(R.yh[i], lo, dy[i]);
+        C.yl[i][t] = lo;
+    }
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
-        df_add(R.th[k], R.tl[k], h * dtau[k]);
-        df_add(R.Ih[k], R.Il[k], h * dI[k]);
+        float tlo = C.tl[k][t], ih = C.Ih[k][t], il = C.Il[k][t];
+        df_add(R.th[k], tlo, __fmul_rn(h, dtau[k]));
+        df_add(ih, il, __fmul_rn(h, dI[k]));
+        C.tl[k][t] = tlo;
+        C.Ih[k][t] = ih;
+        C.Il[k][t] = il;
     }
-    if (R.yh[0] < R.r_stopf) return ODX_CAPTURED;
+    if (R.yh[0] < C.r_stop[t]) return ODX_CAPTURED;
     // escape: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
-    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
+    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
     R.hsf = R.hf;
     return ODX_RUNNING;
@@ -520,10 +636,11 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, const 
 // alive across the FP32 steps would cost 2 x (6 + 2 NF) registers on every step.
 template <int NF>
 __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, RayM<NF> &R,
-                                       float r_isco)
+                                       ColdM<NF> &C, float r_isco)
 {
-    const double a = A.list_mode ? A.rays[4 * R.id + 2] : S.s.a;
-    const double L = df_get(R.Lh, R.Ll);
+    const int t = threadIdx.x;
+    const double a = A.list_mode ? A.rays[4 * C.id[t] + 2] : S.s.a;
+    const double L = df_get(R.Lh, C.Ll[t]);
     const Geo<double> g{a, L, (double)R.sgnf};
     MediumT<double> md{};
     if constexpr (NF > 0) {
@@ -540,31 +657,31 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     }
     double y[6], tau[NF + 1], k1[6], kt1[NF + 1], kI1[NF + 1];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) y[i] = df_get(R.yh[i], R.yl[i]);
+    for (int i = 0; i < 6; ++i) y[i] = df_get(R.yh[i], C.yl[i][t]);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) tau[k] = df_get(R.th[k], R.tl[k]);
+    for (int k = 0; k < NF; ++k) tau[k] = df_get(R.th[k], C.tl[k][t]);
     derivs<double, NF>(g, md, y, tau, k1, kt1, kI1);
     if (R.mode != 1) {  // entering FP64
-        R.hd = (double)R.hf;
-        R.hsd = R.hd;
+        C.hd[t] = (double)R.hf;
+        C.hsd[t] = C.hd[t];
         R.mode = 1;
     }
-    ++R.n64;
-    const double h = R.hd;
+    ++C.n64[t];
+    const double h = C.hd[t];
     double dy[6], e[6], dtau[NF + 1], dI[NF + 1];
     ck_attempt<double, NF>(g, md, y, k1, tau, kt1, kI1, h, dy, e, dtau, dI);
     double errmax = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const double sc = fabs(y[i]) + fabs(R.hsd * k1[i]) + 1e-30;
+        const double sc = fabs(y[i]) + fabs(C.hsd[t] * k1[i]) + 1e-30;
         errmax = fmax(errmax, fabs(e[i] / sc));
     }
     errmax /= S.s.rtol;
     if (isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.0)) {
         ++R.n_rej;
-        R.hd = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);
-        return R.hd < 1e-12 ? ODX_NUMERR : ODX_RUNNING;
+        C.hd[t] = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);
+        return C.hd[t] < 1e-12 ? ODX_NUMERR : ODX_RUNNING;
     }
     ++R.n_acc;
     const double h_next = (errmax > 1.89e-4) ? 0.9 * h * pow(errmax, -0.2) : 5.0 * h;
@@ -574,40 +691,49 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
         float ch[6], cl[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) df_set(ch[i], cl[i], yc[i]);
-        if (on_crossing<NF>(S, R, ch, cl)) return ODX_DISK_HIT;
+        if (on_crossing<NF>(S, R, C, ch, cl)) return ODX_DISK_HIT;
     }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         y[i] += dy[i];
-        df_set(R.yh[i], R.yl[i], y[i]);
+        float lo;
+        df_set(R.yh[i], lo, y[i]);
+        C.yl[i][t] = lo;
     }
 #pragma unroll
     for (int k = 0; k < NF; ++k) {
         tau[k] += dtau[k];
-        df_set(R.th[k], R.tl[k], tau[k]);
-        df_set(R.Ih[k], R.Il[k], df_get(R.Ih[k], R.Il[k]) + dI[k]);
+        float tlo, ih, il;
+        df_set(R.th[k], tlo, tau[k]);
+        df_set(ih, il, df_get(C.Ih[k][t], C.Il[k][t]) + dI[k]);
+        C.tl[k][t] = tlo;
+        C.Ih[k][t] = ih;
+        C.Il[k][t] = il;
     }
-    if (R.yh[0] < R.r_stopf) return ODX_CAPTURED;
+    if (R.yh[0] < C.r_stop[t]) return ODX_CAPTURED;
     // escape test: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
-    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > R.r_startf) return ODX_ESCAPED;
-    R.hd = fmin(h_next, S.s.hmax_frac * y[0]);
-    R.hsd = R.hd;
-    R.hf = (float)R.hd;
+    if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
+    C.hd[t] = fmin(h_next, S.s.hmax_frac * y[0]);
+    C.hsd[t] = C.hd[t];
+    R.hf = (float)C.hd[t];
     return ODX_RUNNING;
 }
 
 // MINB: resident 128-thread blocks per SM the register allocation is capped for.
 template <int NF, int MINB>
-__global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
+__global__ void __launch_bounds__(kMixedBlock, MINB) trace_mixed_kernel(TraceArgs A)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ ColdM<NF> C;
+    // per-warp counters: slots/active written by lane 0 only, the rest by finishing lanes
+    __shared__ unsigned long long wstat[kMixedBlock / 32][6];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (lane < 6) wstat[warp][lane] = 0ull;
+    __syncwarp();
     RayM<NF> R;
     MediumF<NF> mf{};
     bool live = false;
     WarpQueue q;
     q.init(A);
-    unsigned long long my_slots = 0, my_active = 0, my_rays = 0, my_acc = 0, my_rej = 0,
-                       my_64 = 0;
 
     for (;;) {
         int64_t id;
@@ -616,26 +742,33 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
             const int32_t sidx = find_scene(A, id);
             const DevScene &S = A.scenes[sidx];
             const MixedInit m = load80<MixedInit>(A.records + id);
-            R.id = id;
+            C.id[t] = id;
             R.scene = sidx;
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
                 R.yh[state_index(i)] = m.yh[i];
-                R.yl[state_index(i)] = m.yl[i];
+                C.yl[state_index(i)][t] = m.yl[i];
             }
-            R.yh[3] = R.yl[3] = 0.f;
+            R.yh[3] = 0.f;
+            C.yl[3][t] = 0.f;
             R.Lh = m.Lh;
-            R.Ll = m.Ll;
+            C.Ll[t] = m.Ll;
             R.af = m.a;
             R.sgnf = (S.s.convention == ODX_CONV_LITERAL) ? 1.f : -1.f;
             R.r_switch = m.r_switch;
-            R.r_stopf = m.r_stop;
-            R.r_inf = m.r_in;
-            R.r_startf = m.yh[0];
+            C.r_stop[t] = m.r_stop;
+            C.r_in[t] = m.r_in;
+            C.r_start[t] = m.yh[0];
+            C.Ch[t] = m.Ch;
+            C.Cl[t] = m.Cl;
 #pragma unroll
-            for (int k = 0; k < NF + 1; ++k) R.th[k] = R.tl[k] = R.Ih[k] = R.Il[k] = 0.f;
-            R.rch = R.rcl = R.pch = R.pcl = __int_as_float(0x7fc00000);
-            R.n_acc = R.n_rej = R.n_cross = R.n64 = 0;
+            for (int k = 0; k < NF + 1; ++k) {
+                R.th[k] = 0.f;
+                C.tl[k][t] = C.Ih[k][t] = C.Il[k][t] = 0.f;
+            }
+            C.rch[t] = C.rcl[t] = C.pch[t] = C.pcl[t] = __int_as_float(0x7fc00000);
+            R.n_acc = R.n_rej = 0;
+            C.n_cross[t] = C.n64[t] = 0;
             R.hf = m.h0;
             R.hsf = m.h0;
             R.mode = -1;
@@ -645,8 +778,8 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
         const unsigned act = __ballot_sync(kFull, live);
         if (act == 0u) break;
         if (lane == 0) {
-            my_slots += 32;
-            my_active += __popc(act);
+            wstat[warp][4] += 32;
+            wstat[warp][5] += __popc(act);
         }
         // per-lane precision of this step, from the lane's own radius
         const bool want64 = live && (R.yh[0] < R.r_switch);
@@ -658,26 +791,34 @@ __global__ void __launch_bounds__(128, MINB) trace_mixed_kernel(TraceArgs A)
             const DevScene &S = A.scenes[R.scene];
             int32_t status;
             if (run64) {
-                // the FP64 step works on a copy: only this rare path pays for moving the ray
-                // state through local memory, and the FP32 path keeps its registers
-                RayM<NF> t = R;
-                status = step64<NF>(A, S, t, mf.r_isco);
-                R = t;
+                // the FP64 step works on a copy: only this rare path pays for moving the
+                // register state through local memory
+                RayM<NF> r64 = R;
+                status = step64<NF>(A, S, r64, C, mf.r_isco);
+                R = r64;
             } else {
-                status = step32<NF>(S, R, mf);
+                status = step32<NF>(S, R, C, mf);
             }
             if (status == ODX_RUNNING && R.n_acc + R.n_rej >= S.s.max_steps) status = ODX_MAXSTEPS;
             if (status != ODX_RUNNING) {
-                write_slot<NF>(A, S, R, status);
-                my_rays += 1;
-                my_acc += R.n_acc;
-                my_rej += R.n_rej;
-                my_64 += R.n64;
+                write_slot<NF>(A, S, R, C, status);
+                atomicAdd(&wstat[warp][0], 1ull);
+                atomicAdd(&wstat[warp][1], (unsigned long long)R.n_acc);
+                atomicAdd(&wstat[warp][2], (unsigned long long)R.n_rej);
+                atomicAdd(&wstat[warp][3], (unsigned long long)C.n64[t]);
                 live = false;
             }
         }
     }
-    flush_stats(A, lane, my_rays, my_acc, my_rej, my_64, my_slots, my_active);
+    __syncwarp();
+    if (lane == 0) {
+        atomicAdd(&A.stats->rays, wstat[warp][0]);
+        atomicAdd(&A.stats->acc, wstat[warp][1]);
+        atomicAdd(&A.stats->rej, wstat[warp][2]);
+        atomicAdd(&A.stats->fp64, wstat[warp][3]);
+        atomicAdd(&A.stats->slots, wstat[warp][4]);
+        atomicAdd(&A.stats->active, wstat[warp][5]);
+    }
 }
 
 // ---- pass 3: FP64 checks, redshift, intensity, final records -----------------------------
