@@ -307,7 +307,7 @@ int32_t odx_surrogate_render(odx_mlp *mlp, const odx_scene *scene_host, double b
  * is a deployment variant of odx_render.
  *
  * The ray queue counter, the device statistics and the scene table live in one file-scope
- * device array of 28,672 bytes that every GPU loading this library holds until the process
+ * device array of 32,768 bytes that every GPU loading this library holds until the process
  * exits; at most ODX_STATIC_MAX_SCENES scenes per call (more: ODX_ERR_TOO_LARGE, nothing
  * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
  * as odx_render) and the scene descriptions in host memory.  The call works on the calling

@@ -11,7 +11,7 @@
 namespace odx {
 
 constexpr double kSinFloor = 1e-8;  // Section 2.1: sin(theta) floored at 1e-8 near the poles
-constexpr int kFull = 0xffffffff;
+constexpr unsigned kFull = 0xffffffffu;
 
 // Cash-Karp 4(5) tableau (Cash & Karp 1990), the adaptive fifth-order scheme of Section 2.1.
 #define CK_A21 (1.0 / 5.0)
@@ -93,9 +93,9 @@ __device__ __forceinline__ void geodesic_rhs(const Geo<T> &g, T r, T th, T pr, T
 
 // Outer horizon and ISCO radius (prograde for a >= 0) of a disk rotating in +phi
 // (Bardeen, Press & Teukolsky 1972, cited in Section 4.3).
-__device__ __forceinline__ double horizon_radius(double a) { return 1.0 + sqrt(1.0 - a * a); }
+__host__ __device__ __forceinline__ double horizon_radius(double a) { return 1.0 + sqrt(1.0 - a * a); }
 
-__device__ __forceinline__ double isco_radius(double a)
+__host__ __device__ __forceinline__ double isco_radius(double a)
 {
     const double z1 = 1.0 + cbrt(1.0 - a * a) * (cbrt(1.0 + a) + cbrt(1.0 - a));
     const double z2 = sqrt(3.0 * a * a + z1 * z1);
@@ -114,36 +114,42 @@ __device__ __forceinline__ double disk_redshift(double a, double r, double L)
     return 1.0 / (ut * (1.0 - Om * L));
 }
 
+// Observer of one ray: spin, distance, sin and cos of theta_obs and phi_obs,
+// Ro = sqrt(r_obs^2 + a^2), and the image-plane point (alpha, beta).
+struct ObsIn {
+    double a, r_obs, sto, cto, spo, cpo, Ro;
+    double alpha, beta;
+};
+
 // Initial state of the ray through image-plane point (alpha, beta), Section 2.2:
 // Eqs. 18-19 (observer grid -> Cartesian), 20-22 (-> Boyer-Lindquist), 24-26 (velocity of a
 // ray perpendicular to the image plane), 7 (E, then scaled to 1), 8 (L), 4-5 (p_r, p_theta),
 // 13 (Q).  In the physical convention the traced (real) photon moves opposite to Eqs. 24-26.
+// cos(theta) = z'/r and the sine and cosine of phi - phi_obs come from the Cartesian point
+// itself (the same values as the trigonometric functions of Eqs. 21-22, without them).
 struct InitOut {
     double y[6];
     double L, Q;
 };
 
-__device__ __forceinline__ InitOut init_ray(double a, double r_obs, double theta_obs,
-                                            double phi_obs, double alpha, double beta,
-                                            double sgn)
+__device__ __forceinline__ InitOut init_ray(const ObsIn &o, double sgn)
 {
-    double sto, cto, spo, cpo;
-    sincos(theta_obs, &sto, &cto);
-    sincos(phi_obs, &spo, &cpo);
-    const double D = sqrt(r_obs * r_obs + a * a) * sto - beta * cto;
-    const double xp = D * cpo - alpha * spo;
-    const double yp = D * spo + alpha * cpo;
-    const double zp = r_obs * cto + beta * sto;
+    const double a = o.a, sto = o.sto, cto = o.cto;
+    const double D = o.Ro * sto - o.beta * cto;
+    const double xp = D * o.cpo - o.alpha * o.spo;
+    const double yp = D * o.spo + o.alpha * o.cpo;
+    const double zp = o.r_obs * cto + o.beta * sto;
     const double w = xp * xp + yp * yp + zp * zp - a * a;
     const double r = sqrt(0.5 * (w + sqrt(w * w + 4.0 * a * a * zp * zp)));
-    const double th = acos(zp / r);
+    const double c = zp / r;
+    const double th = acos(c);
     const double ph = atan2(yp, xp);
-    double s, c;
-    sincos(th, &s, &c);
-    s = fmax(s, kSinFloor);
+    const double s = fmax(sqrt(fmax((1.0 - c) * (1.0 + c), 0.0)), kSinFloor);
+    const double rho = sqrt(xp * xp + yp * yp);
+    const double cph = rho > 0.0 ? xp / rho : 1.0, sph = rho > 0.0 ? yp / rho : 0.0;
+    const double cP = cph * o.cpo + sph * o.spo;  // cos(phi - phi_obs)
+    const double sP = sph * o.cpo - cph * o.spo;  // sin(phi - phi_obs)
     const double R = sqrt(r * r + a * a);
-    double sP, cP;
-    sincos(ph - phi_obs, &sP, &cP);
     const double Sig = r * r + a * a * c * c;
     const double Del = r * r - 2.0 * r + a * a;
     double rd = sgn * (-(r * R * s * sto * cP + R * R * c * cto) / Sig);
@@ -155,16 +161,16 @@ __device__ __forceinline__ InitOut init_ray(double a, double r_obs, double theta
     rd *= iE;
     td *= iE;
     pd *= iE;
-    InitOut o;
-    o.L = (Sig * Del * pd - 2.0 * a * r) * s * s / (Sig - 2.0 * r);
-    o.y[0] = r;
-    o.y[1] = th;
-    o.y[2] = ph;
-    o.y[3] = 0.0;
-    o.y[4] = Sig * rd / Del;
-    o.y[5] = Sig * td;
-    o.Q = o.y[5] * o.y[5] + (o.L * o.L / (s * s) - a * a) * c * c;
-    return o;
+    InitOut out;
+    out.L = (Sig * Del * pd - 2.0 * a * r) * s * s / (Sig - 2.0 * r);
+    out.y[0] = r;
+    out.y[1] = th;
+    out.y[2] = ph;
+    out.y[3] = 0.0;
+    out.y[4] = Sig * rd / Del;
+    out.y[5] = Sig * td;
+    out.Q = out.y[5] * out.y[5] + (out.L * out.L / (s * s) - a * a) * c * c;
+    return out;
 }
 
 // Relative null violation and relative Carter-constant drift at the end of a ray.

@@ -805,6 +805,7 @@ int32_t odx_surrogate_render(odx_mlp *m, const odx_scene *scene, double band, do
         a.chunk = v.launch.chunk;
         a.persistent = v.launch.persistent;
         a.fp64_batch = v.launch.fp64_batch;
+        set_launch_medium(a, d, true);
         const cudaError_t e = scene->precision == ODX_MIXED
                                   ? launch_trace_mixed(a, 0, v.launch, v.num_sms, st)
                                   : launch_trace_fp64(a, 0, v.launch, v.num_sms, st);

@@ -11,6 +11,7 @@
 #include <thread>
 #include <vector>
 
+#include "kerr_device.cuh"
 #include "odx_internal.h"
 
 namespace odx {
@@ -212,6 +213,7 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     a.chunk = ctx->launch.chunk;
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
+    set_launch_medium(a, ctx->host_scenes[0], n_scenes == 1 || list_mode);
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
     cudaEvent_t ev0, ev1;
     timing_events(ctx, st, &ev0, &ev1);
@@ -265,6 +267,9 @@ int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const odx_scene
     a.chunk = ctx->launch.chunk;
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
+    DevScene d0;
+    fill_dev_scene(d0, scenes[0], 0, 0, 0);
+    set_launch_medium(a, d0, n_scenes == 1);
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
     cudaEvent_t ev0, ev1;
     timing_events(ctx, st, &ev0, &ev1);
@@ -293,6 +298,13 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
     d.ray_begin = ray_begin;
     d.n_rays = n_rays;
     d.img_offset = img_offset;
+    d.o_sto = sin(s.theta_obs);
+    d.o_cto = cos(s.theta_obs);
+    d.o_spo = sin(s.phi_obs);
+    d.o_cpo = cos(s.phi_obs);
+    d.o_Ro = sqrt(s.r_obs * s.r_obs + s.a * s.a);
+    d.o_r_isco = isco_radius(s.a);
+    d.o_r_stop = s.horizon_factor * horizon_radius(s.a);
     d.f_r_out = (float)s.r_out;
     d.f_hmax_frac = (float)s.hmax_frac;
     d.f_rtol32 = (float)s.rtol_fp32;
@@ -308,6 +320,20 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
         const double nu = nf > 0 ? s.freqs[k < nf ? k : nf - 1] : 1.0;
         d.f_nu[k] = (float)nu;
         d.f_inv_nu3[k] = (nu > 0.0) ? (float)(1.0 / (nu * nu * nu)) : 0.f;
+    }
+}
+
+void set_launch_medium(TraceArgs &a, const DevScene &d, bool single)
+{
+    a.single_medium = single ? 1 : 0;
+    a.med.T_index = d.f_T_index;
+    a.med.inv_T0 = d.f_inv_T0;
+    a.med.lr_pref = d.f_lr_pref;
+    a.med.c2_pref = d.f_c2_pref;
+    a.med.pref0 = d.f_pref0;
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) {
+        a.med.nu[k] = d.f_nu[k];
+        a.med.inv_nu3[k] = d.f_inv_nu3[k];
     }
 }
 

@@ -17,6 +17,9 @@ struct DevScene {
     int64_t n_rays;     // n_alpha * n_beta (list mode: n)
     int64_t img_offset; // offset of this scene's image planes, in doubles
     int64_t pad;
+    // FP64 constants of the initial state (Section 2.2) shared by the scene's pixels:
+    // sin, cos of theta_obs and phi_obs, sqrt(r_obs^2 + a^2), r_ISCO and the stop radius
+    double o_sto, o_cto, o_spo, o_cpo, o_Ro, o_r_isco, o_r_stop;
     // FP32 constants of the FP32 stages (filled by fill_dev_scene)
     float f_r_out, f_hmax_frac, f_rtol32;
     float f_T_index;   // 1/T_e = exp(T_index ln r) / T0
@@ -39,6 +42,13 @@ struct DevStats {
     int32_t pad;
 };
 
+// FP32 torus constants of one scene (the f_* fields of DevScene), carried in the kernel
+// parameters when every ray of a launch shares one medium.
+struct MedConst {
+    float T_index, inv_T0, lr_pref, c2_pref, pref0;
+    float nu[ODX_MAX_FREQ], inv_nu3[ODX_MAX_FREQ];
+};
+
 struct TraceArgs {
     const DevScene *scenes;
     int32_t n_scenes;
@@ -52,8 +62,12 @@ struct TraceArgs {
     int32_t chunk;
     int32_t persistent;
     int32_t fp64_batch;
-    int32_t pad;
+    int32_t single_medium;  // 1: every ray uses `med` (one scene, or list mode)
+    MedConst med;
 };
+
+// Fill a.single_medium and a.med from the host copy of scene 0.
+void set_launch_medium(TraceArgs &a, const DevScene &scene0, bool single);
 
 // Launch the FP64 or mixed tracer (with its passes) on `stream`; when ev0/ev1 are given,
 // they are recorded immediately before and after the tracing kernel itself.

@@ -30,7 +30,7 @@ using odx::DevStats;
 constexpr size_t kQueueOffset = 0;
 constexpr size_t kStatsOffset = 64;
 constexpr size_t kScenesOffset = 256;
-constexpr size_t kStaticBytes = 28672;
+constexpr size_t kStaticBytes = 32768;
 static_assert(kScenesOffset + ODX_STATIC_MAX_SCENES * sizeof(DevScene) <= kStaticBytes,
               "scene table does not fit the static scratch");
 static_assert(sizeof(DevStats) <= kScenesOffset - kStatsOffset, "stats do not fit");
@@ -121,6 +121,7 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     a.chunk = launch.chunk;
     a.persistent = launch.persistent;
     a.fp64_batch = launch.fp64_batch;
+    odx::set_launch_medium(a, table[0], n_scenes == 1);
     const int32_t slots = odx::transfer_slots(scenes[0].emitter, scenes[0].n_freq);
     const cudaError_t e =
         scenes[0].precision == ODX_MIXED

@@ -73,26 +73,44 @@ __device__ __forceinline__ int32_t find_scene(const TraceArgs &A, int64_t id)
     return lo;
 }
 
-// Image-plane coordinates and per-ray (a, theta_obs).  Pixel centres:
-// alpha_i = alpha_min + (i + 1/2)(alpha_max - alpha_min)/n_alpha.
-__device__ __forceinline__ void ray_inputs(const TraceArgs &A, const DevScene &S, int64_t id,
-                                           double &alpha, double &beta, double &a,
-                                           double &theta_obs)
+// Observer and image-plane point of ray id.  Pixel centres:
+// alpha_i = alpha_min + (i + 1/2)(alpha_max - alpha_min)/n_alpha.  Grid mode takes the
+// scene's precomputed constants; list mode has its own (alpha, beta, a, cos i) per ray.
+__device__ __forceinline__ ObsIn ray_observer(const TraceArgs &A, const DevScene &S, int64_t id)
 {
+    ObsIn o;
+    o.r_obs = S.s.r_obs;
+    o.spo = S.o_spo;
+    o.cpo = S.o_cpo;
     if (A.list_mode) {
         const double *p = A.rays + 4 * id;
-        alpha = p[0];
-        beta = p[1];
-        a = p[2];
-        theta_obs = acos(p[3]);
+        o.alpha = p[0];
+        o.beta = p[1];
+        o.a = p[2];
+        o.cto = p[3];
+        o.sto = sqrt(fmax((1.0 - p[3]) * (1.0 + p[3]), 0.0));
+        o.Ro = sqrt(o.r_obs * o.r_obs + o.a * o.a);
     } else {
         const int64_t local = id - S.ray_begin;
         const int64_t i = local % S.s.n_alpha, j = local / S.s.n_alpha;
-        alpha = S.s.alpha_min + (((double)i + 0.5) * (S.s.alpha_max - S.s.alpha_min)) / S.s.n_alpha;
-        beta = S.s.beta_min + (((double)j + 0.5) * (S.s.beta_max - S.s.beta_min)) / S.s.n_beta;
-        a = S.s.a;
-        theta_obs = S.s.theta_obs;
+        o.alpha = S.s.alpha_min + (((double)i + 0.5) * (S.s.alpha_max - S.s.alpha_min)) / S.s.n_alpha;
+        o.beta = S.s.beta_min + (((double)j + 0.5) * (S.s.beta_max - S.s.beta_min)) / S.s.n_beta;
+        o.a = S.s.a;
+        o.sto = S.o_sto;
+        o.cto = S.o_cto;
+        o.Ro = S.o_Ro;
     }
+    return o;
+}
+
+// Stop radius and ISCO of a ray's spin (the scene's precomputed values in grid mode).
+__device__ __forceinline__ double ray_r_stop(const TraceArgs &A, const DevScene &S, double a)
+{
+    return A.list_mode ? S.s.horizon_factor * horizon_radius(a) : S.o_r_stop;
+}
+__device__ __forceinline__ double ray_r_isco(const TraceArgs &A, const DevScene &S, double a)
+{
+    return A.list_mode ? isco_radius(a) : S.o_r_isco;
 }
 
 struct RecordOut {

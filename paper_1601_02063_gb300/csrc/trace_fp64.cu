@@ -133,27 +133,28 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
         if (id >= 0) {
             const int32_t sidx = find_scene(A, id);
             const DevScene &S = A.scenes[sidx];
-            double alpha, beta, a, theta_obs;
-            ray_inputs(A, S, id, alpha, beta, a, theta_obs);
+            const ObsIn ob = ray_observer(A, S, id);
+            const double a = ob.a;
             R.id = id;
             R.scene = sidx;
             R.a = a;
             R.sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
-            const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, R.sgn);
+            const InitOut io = init_ray(ob, R.sgn);
 #pragma unroll
             for (int i = 0; i < 6; ++i) R.y[i] = io.y[i];
             R.L = io.L;
             R.Q0 = io.Q;
             R.r_start = io.y[0];
-            R.r_stop = S.s.horizon_factor * horizon_radius(a);
-            R.r_in = (S.s.r_in > 0.0) ? S.s.r_in : isco_radius(a);
+            const double r_isco = ray_r_isco(A, S, a);
+            R.r_stop = ray_r_stop(A, S, a);
+            R.r_in = (S.s.r_in > 0.0) ? S.s.r_in : r_isco;
             R.r_out = S.s.r_out;
             R.r_cross = qnan();
             R.phi_cross = qnan();
             R.n_acc = R.n_rej = R.n_cross = 0;
 #pragma unroll
             for (int k = 0; k < NF + 1; ++k) R.tau[k] = R.I[k] = 0.0;
-            if constexpr (NF > 0) load_medium_t<double>(S, a, m);
+            if constexpr (NF > 0) load_medium_t<double>(S, r_isco, m);
             const Geo<double> g{R.a, R.L, R.sgn};
             derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
             R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);

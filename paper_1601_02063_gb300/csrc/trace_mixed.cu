@@ -29,14 +29,15 @@ struct MixedInit {  // init pass -> tracer
     float yh[5], yl[5];  // r, theta, phi, p_r, p_theta (t starts at 0)
     float Lh, Ll;        // angular momentum
     float r_stop, r_in, r_isco, a;
-    float h0, r_switch;
+    float Qh, Ql;        // Carter constant (Eq. 13), handed on to the finish pass
     float Ch, Cl;        // a^2 - a L (a the FP32 spin) as a pair, for the near-horizon stages
 };
 struct MixedOut {  // tracer -> finish pass
     int32_t status, n_acc, n_rej, n_cross;
-    float rch, rcl, pch, pcl;  // first equatorial crossing r, phi (NaN if none)
-    float yh[5], yl[5];        // final r, theta, phi, p_r, p_theta
-    int32_t n64, pad;
+    float rc, pc;        // first equatorial crossing r, phi (NaN if none)
+    float Lh, Ll;        // angular momentum
+    float yh[5], yl[5];  // final r, theta, phi, p_r, p_theta
+    float Qh, Ql;        // initial Carter constant
 };
 static_assert(sizeof(MixedInit) == sizeof(odx_ray_record), "slot size");
 static_assert(sizeof(MixedOut) == sizeof(odx_ray_record), "slot size");
@@ -89,21 +90,20 @@ __global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= A.n_total) return;
     const DevScene &S = A.scenes[find_scene(A, id)];
-    double alpha, beta, a, theta_obs;
-    ray_inputs(A, S, id, alpha, beta, a, theta_obs);
+    const ObsIn ob = ray_observer(A, S, id);
+    const double a = ob.a;
     const double sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
-    const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, sgn);
+    const InitOut io = init_ray(ob, sgn);
     MixedInit m;
 #pragma unroll
     for (int i = 0; i < 5; ++i) df_set(m.yh[i], m.yl[i], io.y[state_index(i)]);
     df_set(m.Lh, m.Ll, io.L);
-    const double r_isco = isco_radius(a);
-    m.r_stop = (float)(S.s.horizon_factor * horizon_radius(a));
+    df_set(m.Qh, m.Ql, io.Q);
+    const double r_isco = ray_r_isco(A, S, a);
+    m.r_stop = (float)ray_r_stop(A, S, a);
     m.r_in = (float)((S.s.r_in > 0.0) ? S.s.r_in : r_isco);
     m.r_isco = (float)r_isco;
     m.a = (float)a;
-    m.h0 = (float)fmin(S.s.h0, S.s.hmax_frac * io.y[0]);
-    m.r_switch = (float)S.s.r_switch;
     {
         const double af = (double)m.a, Ld = (double)m.Lh + (double)m.Ll;
         df_set(m.Ch, m.Cl, af * af - af * Ld);
@@ -120,7 +120,7 @@ struct RayM {
     float yh[6];       // state high words: r, theta, phi, t, p_r, p_theta
     float th[NF + 1];  // tau high words
     float hf, hsf;     // FP32 step and error-scale step
-    float Lh, af, sgnf, r_switch;
+    float Lh, af, sgnf, r_switch, r_isco;
     int32_t scene, mode, n_acc, n_rej;
 };
 
@@ -134,8 +134,10 @@ struct ColdM {
     float Ih[NF + 1][kMixedBlock], Il[NF + 1][kMixedBlock];
     double hd[kMixedBlock], hsd[kMixedBlock];  // FP64 step and error-scale step
     float Ll[kMixedBlock], r_stop[kMixedBlock], r_start[kMixedBlock], r_in[kMixedBlock];
-    float rch[kMixedBlock], rcl[kMixedBlock], pch[kMixedBlock], pcl[kMixedBlock];
+    float rc[kMixedBlock], pc[kMixedBlock];  // first crossing r, phi
+    float Qh[kMixedBlock], Ql[kMixedBlock];  // initial Carter constant
     float Ch[kMixedBlock], Cl[kMixedBlock];  // a^2 - a L as a pair
+    float k1[6][kMixedBlock];                 // first stage of the current attempt
     long long id[kMixedBlock];
     int32_t n_cross[kMixedBlock], n64[kMixedBlock];
 };
@@ -151,17 +153,17 @@ __device__ __forceinline__ void write_slot(const TraceArgs &A, const DevScene &S
     o.n_acc = R.n_acc;
     o.n_rej = R.n_rej;
     o.n_cross = C.n_cross[t];
-    o.rch = C.rch[t];
-    o.rcl = C.rcl[t];
-    o.pch = C.pch[t];
-    o.pcl = C.pcl[t];
+    o.rc = C.rc[t];
+    o.pc = C.pc[t];
+    o.Lh = R.Lh;
+    o.Ll = C.Ll[t];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         o.yh[i] = R.yh[state_index(i)];
         o.yl[i] = C.yl[state_index(i)][t];
     }
-    o.n64 = C.n64[t];
-    o.pad = 0;
+    o.Qh = C.Qh[t];
+    o.Ql = C.Ql[t];
     store80(A.records + id, o);
     if constexpr (NF > 0) {
         if (A.image) {
@@ -254,18 +256,18 @@ __device__ __noinline__ void locate_crossing64m(const Geo<double> &g, const doub
 }
 
 // FP32 torus constants of one lane's scene (Section 4.2, Eqs. 30-31), folded so that a stage
-// needs one logarithm and two exponentials besides the two per frequency.
+// needs one logarithm and two exponentials besides the two per frequency.  Launches whose
+// rays share one medium read the same fields from the kernel parameters (MedConst).
 template <int NF>
 struct MediumF {
-    float r_isco, T_index, inv_T0, lr_pref, c2_pref, pref0;
+    float T_index, inv_T0, lr_pref, c2_pref, pref0;
     float nu[NF + 1], inv_nu3[NF + 1];
 };
 
 template <int NF>
-__device__ __forceinline__ MediumF<NF> medium_f(const DevScene &S, float r_isco)
+__device__ __forceinline__ MediumF<NF> medium_f(const DevScene &S)
 {
     MediumF<NF> m;
-    m.r_isco = r_isco;
     m.T_index = S.f_T_index;
     m.inv_T0 = S.f_inv_T0;
     m.lr_pref = S.f_lr_pref;
@@ -282,10 +284,6 @@ __device__ __forceinline__ MediumF<NF> medium_f(const DevScene &S, float r_isco)
 // Hardware reciprocal (relative error ~1 ulp; the FP32 stages run at rtol ~1e-6).
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
 
-// FP32 right-hand side of one stage: geodesic (Eqs. 4, 5, 9, 12, 14, 15, with the
-// super-Hamiltonian terms F of the FP64 form) and, for NF > 0, the torus transfer terms
-// (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
-// Frequency slots past the scene's n_freq repeat its last frequency (never written out).
 // Low word of s = fl(x + y) (Knuth two-sum).
 __device__ __forceinline__ float two_sum_err(float x, float y, float s)
 {
@@ -293,10 +291,11 @@ __device__ __forceinline__ float two_sum_err(float x, float y, float s)
     return (x - (s - bp)) + (y - bp);
 }
 
-// Where the low words of the stage inputs r, p_r come from, for the near-horizon stages:
-// r = y0r + tr (rounded) with the state's low word ylr; p_r likewise.
+// How the stage inputs r, theta, p_r were formed: r = fl(y0r + tr) with tr = fl(h acc_r),
+// and so on; with the state's low words (in shared memory) they give the stage inputs as
+// pairs where the near-horizon and near-pole stages need them.
 struct PairStage {
-    float y0r, tr, ylr, y0t, tt, ylt, y0p, tp, ylp, Ch, Cl;
+    float y0r, tr, y0t, tt, y0p, tp;
 };
 
 // sin and cos of theta = hi + lo near a pole (|sin theta| < 1/4).  There the FP32 stage
@@ -327,11 +326,14 @@ __device__ __forceinline__ void sincos_pole(float hi, float lo, float &s, float 
 // it dp_theta/ds, noise of order one there, which stalls the step control of rays with small
 // p_theta.  In that region Delta, Delta p_r - P and so F are formed in float-pair arithmetic
 // from the stage inputs' low words.
+template <class Cold>
 __device__ __forceinline__ void near_horizon(float r, float pr, float a, const PairStage &ps,
-                                             float &Del, float &D, float &S)
+                                             const Cold &C, float &Del, float &D, float &S)
 {
-    const float rl = two_sum_err(ps.y0r, ps.tr, r) + ps.ylr;
-    const float pl = two_sum_err(ps.y0p, ps.tp, pr) + ps.ylp;
+    const int t = threadIdx.x;
+    const float rl = two_sum_err(ps.y0r, ps.tr, r) + C.yl[0][t];
+    const float pl = two_sum_err(ps.y0p, ps.tp, pr) + C.yl[4][t];
+    const float Ch = C.Ch[t], Cl = C.Cl[t];
     const float q2 = __fmul_rn(r, r);  // r^2 = q2 + q2e (products kept out of contractions)
     const float q2e = fmaf(2.f * r, rl, fmaf(r, r, -q2));
     const float a2h = __fmul_rn(a, a), a2l = fmaf(a, a, -a2h);
@@ -339,29 +341,34 @@ __device__ __forceinline__ void near_horizon(float r, float pr, float a, const P
     const float d1 = q2 - 2.f * r;
     float Dh = d1 + a2h;
     float Dl = two_sum_err(d1, a2h, Dh) + q2e - 2.f * rl + a2l;
-    const float t = Dh + Dl;
-    Dl = Dl - (t - Dh);
-    Dh = t;
+    const float Ds = Dh + Dl;
+    Dl = Dl - (Ds - Dh);
+    Dh = Ds;
     // u = Delta p_r, P = r^2 + (a^2 - a L), D = u - P
     const float uh = __fmul_rn(Dh, pr);
     const float ul = fmaf(Dl, pr, fmaf(Dh, pl, fmaf(Dh, pr, -uh)));
-    const float Ph = q2 + ps.Ch;
-    const float Pl = two_sum_err(q2, ps.Ch, Ph) + q2e + ps.Cl;
+    const float Ph = q2 + Ch;
+    const float Pl = two_sum_err(q2, Ch, Ph) + q2e + Cl;
     const float dh = uh - Ph;
     D = dh + (two_sum_err(uh, -Ph, dh) + (ul - Pl));
     S = uh + Ph;
     Del = Dh;
 }
 
-template <int NF>
-__device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> &m,
-                                         const float *in, const PairStage &ps, float f[6],
-                                         float *ft, float *fI)
+// FP32 right-hand side of one stage: geodesic (Eqs. 4, 5, 9, 12, 14, 15, with the
+// super-Hamiltonian terms F of the FP64 form) and, for NF > 0, the torus transfer terms
+// (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
+// Frequency slots past the scene's n_freq repeat its last frequency (never written out).
+template <int NF, class Med, class Cold>
+__device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, float r_isco,
+                                         const float *in, const PairStage &ps, const Cold &C,
+                                         float f[6], float *ft, float *fI)
 {
     const float r = in[0], pr = in[2], pth = in[3];
     float s, c;
     __sincosf(in[1], &s, &c);  // |x| <= pi up to pole passages: abs. error <= 2^-21.4
-    if (fabsf(s) < 0.25f) sincos_pole(in[1], two_sum_err(ps.y0t, ps.tt, in[1]) + ps.ylt, s, c);
+    if (fabsf(s) < 0.25f)
+        sincos_pole(in[1], two_sum_err(ps.y0t, ps.tt, in[1]) + C.yl[1][threadIdx.x], s, c);
     s = fmaxf(s, 1e-8f);
     const float a = g.a, L = g.L;
     const float r2 = r * r, a2 = a * a, s2 = s * s;
@@ -369,7 +376,7 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> 
     float Del = r2 - 2.f * r + a2;
     const bool nh = Del < 0.25f * r2;
     float Dm = 0.f, Sm = 0.f;  // Delta p_r -+ P (near the horizon)
-    if (nh) near_horizon(r, pr, a, ps, Del, Dm, Sm);
+    if (nh) near_horizon(r, pr, a, ps, C, Del, Dm, Sm);
     const float iSD = rcp_fast(Sig * Del);
     const float iS = Del * iSD;
     const float iD = Sig * iSD;
@@ -383,13 +390,14 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> 
     const float kap = pth2 + L * L * is2 + a2 * s2;
     const float rm1 = r - 1.f;
     const float twor = 2.f * r;
-    f[0] = g.sgn * (Del * pr * iS);
-    f[1] = g.sgn * (pth * iS);
-    f[2] = g.sgn * ((twor * a + (Sig - twor) * L * is2) * iSD);
-    f[3] = g.sgn * (1.f + (twor * rr - twor * a * L) * iSD);
-    f[4] = g.sgn * ((-kap * rm1 + twor * rr - 2.f * a * L) * iSD - 2.f * pr2 * rm1 * iS +
-                    F * (rm1 * iSD + r * iS * iS));
-    f[5] = g.sgn * (s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS);
+    // the direction sign sgn is carried by the geodesic step size (h_geo = sgn h)
+    f[0] = Del * pr * iS;
+    f[1] = pth * iS;
+    f[2] = (twor * a + (Sig - twor) * L * is2) * iSD;
+    f[3] = 1.f + (twor * rr - twor * a * L) * iSD;
+    f[4] = (-kap * rm1 + twor * rr - 2.f * a * L) * iSD - 2.f * pr2 * rm1 * iS +
+           F * (rm1 * iSD + r * iS * iS);
+    f[5] = s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS;
     if constexpr (NF > 0) {
         // Keplerian flow where r >= r_ISCO and timelike, else ZAMO; 1/g = u^t (1 - Omega L)
         const float A = rr * rr - a2 * Del * s2;
@@ -398,7 +406,7 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const MediumF<NF> 
         const float gpp = A * s2 * iS;
         float Om = rcp_fast(r * r * rsqrtf(r) + a);
         float N = gtt + 2.f * gtp * Om + gpp * Om * Om;
-        if (!(r >= m.r_isco && N < 0.f)) {  // ZAMO: g_tt - g_tphi^2 / g_phiphi = -Sigma Delta / A
+        if (!(r >= r_isco && N < 0.f)) {  // ZAMO: g_tt - g_tphi^2 / g_phiphi = -Sigma Delta / A
             const float iA = rcp_fast(A);
             Om = twor * a * iA;
             N = -Sig * Del * iA;
@@ -439,10 +447,8 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, Cold
     const int t = threadIdx.x;
     const int n = ++C.n_cross[t];
     if (n == 1) {
-        C.rch[t] = ch[0];
-        C.rcl[t] = cl[0];
-        C.pch[t] = ch[2];
-        C.pcl[t] = cl[2];
+        C.rc[t] = ch[0];
+        C.pc[t] = ch[2];
     }
     if (S.s.emitter == ODX_EMIT_THIN_DISK && ch[0] >= C.r_in[t] && ch[0] <= S.f_r_out) {
 #pragma unroll
@@ -463,9 +469,9 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, Cold
 // sum and the error estimate, so no stage derivative is kept; t and phi, which no
 // right-hand side reads, enter only those two sums.  The first stage is evaluated afresh
 // at every attempt (a rejected attempt repeats it exactly).
-template <int NF>
+template <int NF, class Med>
 __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<NF> &C,
-                                          const MediumF<NF> &mf)
+                                          const Med &mf)
 {
     const int t = threadIdx.x;
     constexpr int NG = 4 + NF;  // stage inputs: r, theta, p_r, p_theta, tau_k
@@ -476,6 +482,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
         R.mode = 0;
     }
     const float h = R.hf;
+    const float hg = R.sgnf * h;  // geodesic components: dy/ds = sgn f
     float y0[NG];
     y0[0] = R.yh[0];
     y0[1] = R.yh[1];
@@ -486,17 +493,16 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     float in[NG];
 #pragma unroll
     for (int c = 0; c < NG; ++c) in[c] = y0[c];
-    PairStage ps{y0[0], 0.f, C.yl[0][t], y0[1], 0.f, C.yl[1][t], y0[2], 0.f, C.yl[4][t],
-                 C.Ch[t], C.Cl[t]};
-    float acc[5][NG], k1[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
+    PairStage ps{y0[0], 0.f, y0[1], 0.f, y0[2], 0.f};
+    float acc[5][NG], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
 
 #define ODX_ACC(J, COEF)                                                   \
     _Pragma("unroll") for (int c = 0; c < NG; ++c) acc[J][c] = fmaf((float)(COEF), kf[c], acc[J][c]);
 #define ODX_NEXT(J)                                                        \
-    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(h, acc[J][c], y0[c]); \
-    ps.tr = __fmul_rn(h, acc[J][0]);                                       \
-    ps.tt = __fmul_rn(h, acc[J][1]);                                       \
-    ps.tp = __fmul_rn(h, acc[J][2]);                                       \
+    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(c < 4 ? hg : h, acc[J][c], y0[c]); \
+    ps.tr = __fmul_rn(hg, acc[J][0]);                                      \
+    ps.tt = __fmul_rn(hg, acc[J][1]);                                      \
+    ps.tp = __fmul_rn(hg, acc[J][2]);                                      \
     in[0] = __fadd_rn(y0[0], ps.tr);                                       \
     in[1] = __fadd_rn(y0[1], ps.tt);                                       \
     in[2] = __fadd_rn(y0[2], ps.tp);
@@ -513,7 +519,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 #pragma unroll 1
     for (int st = 0; st < 6; ++st) {
         float f[6], ft[NF + 1], fI[NF + 1];
-        derivs32<NF>(g, mf, in, ps, f, ft, fI);
+        derivs32<NF>(g, mf, R.r_isco, in, ps, C, f, ft, fI);
         float kf[NG];
         kf[0] = f[0];
         kf[1] = f[1];
@@ -533,7 +539,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                k1[i] = f[i];
+                C.k1[i][t] = R.sgnf * f[i];
                 dy[i] = (float)CK_B1 * f[i];
                 e[i] = (float)CK_E1 * f[i];
             }
@@ -582,8 +588,8 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     float errmax = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * k1[i]) + 1e-30f;
-        errmax = fmaxf(errmax, __fdividef(fabsf(h * e[i]), sc));
+        const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * C.k1[i][t]) + 1e-30f;
+        errmax = fmaxf(errmax, __fdividef(fabsf(hg * e[i]), sc));
     }
     errmax = __fdividef(errmax, S.f_rtol32);
     if (isnan(errmax)) errmax = INFINITY;
@@ -595,15 +601,18 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     ++R.n_acc;
     const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dy[i] = __fmul_rn(dy[i], h);  // rounded before the two-sums
+    for (int i = 0; i < 6; ++i) dy[i] = __fmul_rn(dy[i], hg);  // rounded before the two-sums
     {
         float nh = R.yh[1], nl = C.yl[1][t];
         const bool c0 = cos_positive(nh, nl);
         df_add(nh, nl, dy[1]);
         if (c0 != cos_positive(nh, nl)) {
-            float yl[6], ch[6], cl[6];
+            float yl[6], k1[6], ch[6], cl[6];
 #pragma unroll
-            for (int i = 0; i < 6; ++i) yl[i] = C.yl[i][t];
+            for (int i = 0; i < 6; ++i) {
+                yl[i] = C.yl[i][t];
+                k1[i] = C.k1[i][t];
+            }
             locate_crossing32(g, R.yh, yl, k1, h, ch, cl);
             if (on_crossing<NF>(S, R, C, ch, cl)) return ODX_DISK_HIT;
         }
@@ -720,8 +729,11 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
 }
 
 // MINB: resident 128-thread blocks per SM the register allocation is capped for.
-template <int NF, int MINB>
-__global__ void __launch_bounds__(kMixedBlock, MINB) trace_mixed_kernel(TraceArgs A)
+// SINGLE: every ray shares the launch's medium (A.med, read from the kernel parameters, no
+// registers); otherwise each lane keeps its scene's constants.
+template <int NF, int MINB, bool SINGLE>
+__global__ void __launch_bounds__(kMixedBlock, MINB)
+    trace_mixed_kernel(const __grid_constant__ TraceArgs A)
 {
     __shared__ ColdM<NF> C;
     // per-warp counters: slots/active written by lane 0 only, the rest by finishing lanes
@@ -755,7 +767,7 @@ __global__ void __launch_bounds__(kMixedBlock, MINB) trace_mixed_kernel(TraceArg
             C.Ll[t] = m.Ll;
             R.af = m.a;
             R.sgnf = (S.s.convention == ODX_CONV_LITERAL) ? 1.f : -1.f;
-            R.r_switch = m.r_switch;
+            R.r_switch = (float)S.s.r_switch;
             C.r_stop[t] = m.r_stop;
             C.r_in[t] = m.r_in;
             C.r_start[t] = m.yh[0];
@@ -766,13 +778,16 @@ __global__ void __launch_bounds__(kMixedBlock, MINB) trace_mixed_kernel(TraceArg
                 R.th[k] = 0.f;
                 C.tl[k][t] = C.Ih[k][t] = C.Il[k][t] = 0.f;
             }
-            C.rch[t] = C.rcl[t] = C.pch[t] = C.pcl[t] = __int_as_float(0x7fc00000);
+            C.rc[t] = C.pc[t] = __int_as_float(0x7fc00000);
+            C.Qh[t] = m.Qh;
+            C.Ql[t] = m.Ql;
             R.n_acc = R.n_rej = 0;
             C.n_cross[t] = C.n64[t] = 0;
-            R.hf = m.h0;
-            R.hsf = m.h0;
+            R.hf = fminf((float)S.s.h0, S.f_hmax_frac * m.yh[0]);
+            R.hsf = R.hf;
             R.mode = -1;
-            mf = medium_f<NF>(S, m.r_isco);
+            R.r_isco = m.r_isco;
+            if constexpr (!SINGLE) mf = medium_f<NF>(S);
             live = true;
         }
         const unsigned act = __ballot_sync(kFull, live);
@@ -794,10 +809,13 @@ __global__ void __launch_bounds__(kMixedBlock, MINB) trace_mixed_kernel(TraceArg
                 // the FP64 step works on a copy: only this rare path pays for moving the
                 // register state through local memory
                 RayM<NF> r64 = R;
-                status = step64<NF>(A, S, r64, C, mf.r_isco);
+                status = step64<NF>(A, S, r64, C, R.r_isco);
                 R = r64;
             } else {
-                status = step32<NF>(S, R, C, mf);
+                if constexpr (SINGLE)
+                    status = step32<NF>(S, R, C, A.med);
+                else
+                    status = step32<NF>(S, R, C, mf);
             }
             if (status == ODX_RUNNING && R.n_acc + R.n_rej >= S.s.max_steps) status = ODX_MAXSTEPS;
             if (status != ODX_RUNNING) {
@@ -828,10 +846,8 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     if (id >= A.n_total) return;
     const DevScene &S = A.scenes[find_scene(A, id)];
     const MixedOut o = load80<MixedOut>(A.records + id);
-    double alpha, beta, a, theta_obs;
-    ray_inputs(A, S, id, alpha, beta, a, theta_obs);
-    const double sgn = (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0;
-    const InitOut io = init_ray(a, S.s.r_obs, theta_obs, S.s.phi_obs, alpha, beta, sgn);
+    const double a = A.list_mode ? A.rays[4 * id + 2] : S.s.a;
+    const double L = df_get(o.Lh, o.Ll), Q0 = df_get(o.Qh, o.Ql);
     double yend[6];
 #pragma unroll
     for (int i = 0; i < 5; ++i) yend[state_index(i)] = df_get(o.yh[i], o.yl[i]);
@@ -841,16 +857,16 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     r.n_acc = o.n_acc;
     r.n_rej = o.n_rej;
     r.n_cross = o.n_cross;
-    r.r_cross = df_get(o.rch, o.rcl);
-    r.phi_cross = df_get(o.pch, o.pcl);
-    r.H_end = null_violation(a, io.L, yend);
-    r.Q_drift = (carter_q(a, io.L, yend) - io.Q) / fmax(fabs(io.Q), 1.0);
+    r.r_cross = (double)o.rc;
+    r.phi_cross = (double)o.pc;
+    r.H_end = null_violation(a, L, yend);
+    r.Q_drift = (carter_q(a, L, yend) - Q0) / fmax(fabs(Q0), 1.0);
     r.r_hit = r.phi_hit = r.g = qnan();
     r.intensity = 0.0;
     if (o.status == ODX_DISK_HIT) {
         r.r_hit = yend[0];
         r.phi_hit = yend[2];
-        r.g = disk_redshift(a, yend[0], io.L);
+        r.g = disk_redshift(a, yend[0], L);
         const double g2 = r.g * r.g;
         r.intensity = g2 * g2 * pow(yend[0], -S.s.q_emis);
     }
@@ -869,16 +885,26 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     }
 }
 
-template <int NF>
+template <int NF, bool SINGLE>
 cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 grid, cudaStream_t st)
 {
     const dim3 block(L.block);
     switch (L.blocks_per_sm <= 2 ? 2 : (L.blocks_per_sm >= 4 ? 4 : 3)) {
-    case 2: trace_mixed_kernel<NF, 2><<<grid, block, 0, st>>>(args); break;
-    case 3: trace_mixed_kernel<NF, 3><<<grid, block, 0, st>>>(args); break;
-    default: trace_mixed_kernel<NF, 4><<<grid, block, 0, st>>>(args); break;
+    case 2: trace_mixed_kernel<NF, 2, SINGLE><<<grid, block, 0, st>>>(args); break;
+    case 3: trace_mixed_kernel<NF, 3, SINGLE><<<grid, block, 0, st>>>(args); break;
+    default: trace_mixed_kernel<NF, 4, SINGLE><<<grid, block, 0, st>>>(args); break;
     }
     return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 grid, cudaStream_t st)
+{
+    if constexpr (NF == 0)  // no medium
+        return launch_mixed_nf<NF, true>(args, L, grid, st);
+    else
+        return args.single_medium ? launch_mixed_nf<NF, true>(args, L, grid, st)
+                                  : launch_mixed_nf<NF, false>(args, L, grid, st);
 }
 
 cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,

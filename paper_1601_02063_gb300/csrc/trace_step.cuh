@@ -55,7 +55,7 @@ struct MediumT {
 };
 
 template <typename T>
-__device__ __forceinline__ void load_medium_t(const DevScene &S, double a, MediumT<T> &m)
+__device__ __forceinline__ void load_medium_t(const DevScene &S, double r_isco, MediumT<T> &m)
 {
     m.ne_index = (T)S.s.ne_index;
     m.inv_2w2 = (T)(1.0 / (2.0 * S.s.theta_width * S.s.theta_width));
@@ -63,7 +63,7 @@ __device__ __forceinline__ void load_medium_t(const DevScene &S, double a, Mediu
     m.inv_T0 = (T)(1.0 / S.s.T0);
     m.T_index = (T)S.s.T_index;
     m.C_norm = (T)S.s.C_norm;
-    m.r_isco = (T)isco_radius(a);
+    m.r_isco = (T)r_isco;
     m.n_freq = S.s.n_freq;
 #pragma unroll
     for (int k = 0; k < ODX_MAX_FREQ; ++k) m.freqs[k] = (T)S.s.freqs[k];
