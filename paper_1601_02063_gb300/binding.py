@@ -7,6 +7,7 @@ the CUDA library has not been built; there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import functools
 import os
 
 import numpy as np
@@ -221,8 +222,16 @@ def odx_sync(ctx, stream: int | None = None, timeout_s: float = 600.0) -> None:
     _check(ctx, lib().odx_sync(ctx, stream or None, timeout_s), "odx_sync")
 
 
-def odx_torus_norm(a, nu=1.0, ne_index=1.5, T0=10.0, T_index=0.84, r_outer=1000.0) -> float:
+@functools.lru_cache(maxsize=256)
+def _torus_norm(a, nu, ne_index, T0, T_index, r_outer) -> float:
     return lib().odx_torus_norm(a, nu, ne_index, T0, T_index, r_outer)
+
+
+def odx_torus_norm(a, nu=1.0, ne_index=1.5, T0=10.0, T_index=0.84, r_outer=1000.0) -> float:
+    """Emissivity normalisation (a pure function of its arguments: memoised, so that
+    scene structs built per call cost no quadrature)."""
+    return _torus_norm(float(a), float(nu), float(ne_index), float(T0), float(T_index),
+                       float(r_outer))
 
 
 def odx_fma_peak(ctx, precision: str) -> float:
