@@ -50,6 +50,16 @@ def flops_per_step(scene: dict) -> float:
     return f
 
 
+def measured_peak(key):
+    """A measured peak of the GB300s (None if the file is absent)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
+
+
 def read_traffic(workload, precision):
     """DRAM bytes per launch of the tracer from the committed ncu summary (None if the
     kernel has no capture for this workload)."""
@@ -386,6 +396,15 @@ def run_ours(args):
             holder["r"] = sg.render(sc, out=out_s[:3])
         ms_s = timed(surr, 3)
         img_s, _, _, m_fb = holder["r"]
+        # the network alone on the image's 2048^2 input rows (tcgen05 inference kernel)
+        mlp_flops = 2.0 * (4 * 256 + 3 * 256 * 256 + 256 * 4) * n2
+        xin = torch.rand((n2, 4), dtype=torch.float32, device=f"cuda:{local}")
+        yout = torch.empty((n2, 4), dtype=torch.float32, device=f"cuda:{local}")
+        B.odx_mlp_forward(sg.mlp, xin.data_ptr(), n2, yout.data_ptr(), stream.cuda_stream)
+        ms_mlp = timed(lambda: B.odx_mlp_forward(sg.mlp, xin.data_ptr(), n2, yout.data_ptr(),
+                                                 stream.cuda_stream), 5)
+        peak_bf16 = measured_peak("bf16_tflops")
+        del xin, yout
         surrogate = {
             "workload": "thin disk 2048x2048, a=0.7, i=45 deg, [-20,20]^2",
             "training": {"rays": 1 << 23, "steps": len(loss), "seconds": t_train,
@@ -395,7 +414,13 @@ def run_ours(args):
             "mixed_integrator": {"ms_per_image": ms_mixed, "images_per_s": 1e3 / ms_mixed,
                                  "image_error_vs_fp64": err_mixed},
             "fp64_integrator": {"ms_per_image": ms64, "images_per_s": 1e3 / ms64},
-            "mlp_flops_per_image": 2.0 * (4 * 256 + 3 * 256 * 256 + 256 * 4) * n2,
+            "mlp_flops_per_image": mlp_flops,
+            "mlp_inference": {
+                "kernel": "mlp_forward_tc (tcgen05, accumulator in tensor memory)",
+                "ms_per_image": ms_mlp, "achieved_tflops": mlp_flops / ms_mlp / 1e9,
+                "peak_tflops": peak_bf16, "frac": (mlp_flops / ms_mlp / 1e9 / peak_bf16)
+                if peak_bf16 else None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 burst)"},
         }
         sg.close()
         del rec2, img2, ref64, out_s

@@ -270,7 +270,11 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
 int32_t odx_mlp_destroy(odx_mlp *mlp);
 int32_t odx_mlp_get_params(odx_mlp *mlp, float *params_host);
 int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Adam state */
-/* y_dev[n][4] = MLP(x_dev[n][4]), any n (processed in chunks of max_batch). */
+/* y_dev[n][4] = MLP(x_dev[n][4]), any n, on the tensor cores (tcgen05: 128-row tiles, the
+ * FP32 accumulator in tensor memory); x_dev and y_dev 16-byte aligned (else INVALID_ARG).
+ * Asynchronous on `stream`.  A tensor-core wait that times out leaves its tile's outputs
+ * unwritten and raises a device flag, reported (and cleared) as ODX_ERR_DEVICE_FLAG by the
+ * next odx_mlp_get_params or odx_surrogate_render call. */
 int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
 /* Loss and gradients (dL/dparams, layout as the parameters) of one batch, n a multiple of
  * 128 and <= max_batch; synchronous, results copied to host (either may be NULL). */

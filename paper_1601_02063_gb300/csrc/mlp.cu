@@ -1,8 +1,9 @@
 // Learned thin-disk transfer function (alpha, beta, a, cos i) -> (capture logit, log r_cross,
 // phi_cross / pi, g): 4 -> 256 -> 256 -> 256 -> 256 -> 4 with SiLU, BF16 weights and
-// activations, FP32 accumulation.  Training (forward, backward, Adam) and inference run in
-// the kernels below; the 256 x 256 layers use the BF16 tensor-core GEMM of mlp_gemm.cuh,
-// the 4-wide input and output layers are CUDA-core kernels.  The surrogate render
+// activations, FP32 accumulation.  Training (forward, backward, Adam) runs in the kernels
+// below, the 256 x 256 layers on the BF16 mma.sync GEMM of mlp_gemm.cuh and the 4-wide input
+// and output layers on CUDA cores; inference is one fused kernel per 128-row tile on the
+// tcgen05 tensor cores (mlp_forward_tc, accumulator in tensor memory).  The surrogate render
 // classifies each pixel and hands the uncertain ones (near the Bardeen critical curve or
 // with an unsure capture probability) back to the ray tracer.
 #include <cuda_bf16.h>
@@ -17,6 +18,7 @@
 #include "kerr_device.cuh"
 #include "mlp_gemm.cuh"
 #include "odx_internal.h"
+#include "tcgen05.cuh"
 
 namespace odx {
 int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes);
@@ -64,6 +66,9 @@ struct odx_mlp {
     bf16 *dZ = nullptr, *dZ2 = nullptr;
     float *Y = nullptr, *dY = nullptr, *loss = nullptr;
     float *xin = nullptr;   // padded input rows for inference
+    bf16 *wpack = nullptr;  // hidden-layer weights in the tensor-core operand layout
+    int *tc_err = nullptr;  // set by the inference kernel if a wait timed out
+    int num_sms = 0;
     // surrogate render workspace
     int64_t surr_cap = 0;
     float *surr_x = nullptr, *surr_y = nullptr;
@@ -418,113 +423,277 @@ __global__ void scatter_fallback(const odx_ray_record *__restrict__ rec,
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// ---- fused inference: all five layers of a 128-row tile in one CTA --------------------------
-// Activations stay in shared memory (128 x 256 BF16, padded rows); each 256 x 256 layer
-// streams its BF16 weights from L2 in 32-row chunks (cp.async, double-buffered) and runs
-// mma.sync m16n8k16 with 16 warps tiled 4 (rows) x 4 (columns) over 32 x 64 each; bias and
-// SiLU are applied to the FP32 accumulators before the BF16 result overwrites the tile.
-constexpr int FZ_ROWS = 128, FZ_THREADS = 512, FZ_LDH = HID + 8, FZ_KC = 32;
-constexpr size_t FZ_SMEM = (size_t)(FZ_ROWS * FZ_LDH + 2 * FZ_KC * FZ_LDH) * sizeof(bf16);
+// ---- inference on the fifth-generation tensor cores (tcgen05) ------------------------------
+// One CTA per SM walks 128-row tiles.  Per tile: layer 1 (4 -> 256) on CUDA cores into the
+// activation tile A (shared memory, BF16, K-major core-matrix layout); for each 256 x 256
+// layer the weights W_l^T (packed once into the same layout, 128 KB) arrive by bulk copy,
+// one thread issues 16 MMAs of 128 x 256 x 16 with the FP32 accumulator in tensor memory
+// (256 of its 512 columns), the warps read the accumulator back (bias + SiLU, BF16) into A,
+// or, after the last hidden layer, straight into the 256 -> 4 dot products.  The next
+// layer's weights are loaded while the epilogue runs.  Every wait is bounded: on a time-out
+// the kernel flags *err, waits (bounded) for its own copies and MMAs, frees its tensor
+// memory and returns.
+constexpr int TC_THREADS = 512, TC_ROWS = 128, TC_CG = TC_THREADS / TC_ROWS;  // column groups
+constexpr int TC_COLS = HID / TC_CG;  // columns of one row per thread (64)
+constexpr uint32_t TC_A_BYTES = TC_ROWS * HID * 2, TC_B_BYTES = HID * HID * 2;
+constexpr uint32_t TC_TMEM_COLS = 256;
+constexpr uint32_t TC_WAIT = 1u << 20;
+// small operands staged in shared memory: W1^T as float4 per column, biases b1..b4,
+// W5 as float4 per input column, b5; layer-5 partial sums of column groups 1..3
+constexpr size_t TC_CONST_BYTES = (HID * 4 + 4 * HID + HID * 4 + 4) * sizeof(float);
+constexpr size_t TC_RED_BYTES = (size_t)(TC_CG - 1) * TC_ROWS * NOUT * sizeof(float);
+constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_B_BYTES + TC_CONST_BYTES + TC_RED_BYTES + 64;
+static_assert(TC_SMEM <= 232448, "shared memory of one CTA");
 
-__global__ void __launch_bounds__(FZ_THREADS, 1)
-    mlp_fused_forward(const float *__restrict__ x, const bf16 *__restrict__ pb,
-                      const float *__restrict__ p, int64_t n_rows, float *__restrict__ y)
+// Hidden-layer weights W_l[k][n] (FP32 master's BF16 copy) -> B operand B[n][k] in the
+// K-major core-matrix layout, one 128 KB block per layer.
+__global__ void pack_hidden_weights(const bf16 *__restrict__ pb, bf16 *__restrict__ wpack)
 {
-    extern __shared__ __align__(16) unsigned char fz_smem[];
-    bf16 *sH = reinterpret_cast<bf16 *>(fz_smem);
-    bf16 *sW = sH + FZ_ROWS * FZ_LDH;  // [2][FZ_KC][FZ_LDH]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 2, wn = warp & 3;  // 4 x 4 warps, 32 x 64 each
-    const int64_t row0 = (int64_t)blockIdx.x * FZ_ROWS;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 3 * HID * HID) return;
+    const int l = 2 + idx / (HID * HID), e = idx % (HID * HID);
+    const int n = e / HID, k = e % HID;
+    wpack[(size_t)(l - 2) * HID * HID + tc::kmajor_offset(n, k, HID) / 2] =
+        pb[off_w(l) + k * HID + n];
+}
 
-    // layer 1 on CUDA cores: 128 x 256 outputs, 64 per thread
-    for (int i = tid; i < FZ_ROWS * HID; i += FZ_THREADS) {
-        const int r = i / HID, nn = i % HID;
-        const int64_t gr = row0 + r;
-        float z = p[OFF_B1 + nn];
-        if (gr < n_rows) {
-#pragma unroll
-            for (int k = 0; k < NIN; ++k) z += x[gr * NIN + k] * bfv(pb, OFF_W1 + k * HID + nn);
-        }
-        sH[r * FZ_LDH + nn] = __float2bfloat16_rn(silu(z));
-    }
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
 
-    const int j8 = lane >> 3, r8 = lane & 7, g = lane >> 2, q = lane & 3;
-    for (int l = 2; l <= 4; ++l) {
-        const bf16 *W = pb + off_w(l);
-        auto load_chunk = [&](int buf, int kc) {
-            // 32 rows x 256 columns = 1024 16-byte chunks, 2 per thread
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int chunk = tid + c * FZ_THREADS;
-                const int r = chunk >> 5, cc = (chunk & 31) * 8;
-                cp_async16(&sW[(buf * FZ_KC + r) * FZ_LDH + cc], W + (size_t)(kc * FZ_KC + r) * HID + cc);
-            }
-            cp_async_commit();
-        };
-        float acc[2][8][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.f;
-        __syncthreads();  // previous layer's tile complete
-        load_chunk(0, 0);
-        for (int kc = 0; kc < HID / FZ_KC; ++kc) {
-            const int buf = kc & 1;
-            if (kc + 1 < HID / FZ_KC) {
-                load_chunk(buf ^ 1, kc + 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            const bf16 *wb = sW + buf * FZ_KC * FZ_LDH;
-#pragma unroll
-            for (int ks = 0; ks < FZ_KC; ks += 16) {
-                uint32_t af[2][4], bfr[4][4];
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-                    ldsm_x4(af[i], sH + (wm * 32 + i * 16 + (lane & 15)) * FZ_LDH + kc * FZ_KC + ks +
-                                       (lane >> 4) * 8);
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    ldsm_x4_t(bfr[jj], wb + (ks + r8 + (j8 & 1) * 8) * FZ_LDH + wn * 64 + jj * 16 +
-                                           (j8 >> 1) * 8);
-#pragma unroll
-                for (int i = 0; i < 2; ++i)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        mma_bf16(acc[i][j], af[i], bfr[j >> 1][(j & 1) * 2], bfr[j >> 1][(j & 1) * 2 + 1]);
-            }
-            __syncthreads();  // chunk buffer and tile reads done before they are overwritten
-        }
-        // epilogue: bias + SiLU, BF16 result replaces the tile
-        const float *bias = p + off_b(l);
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int r = wm * 32 + i * 16 + g + h * 8;
-                    const int nn = wn * 64 + j * 8 + 2 * q;
-                    const float z0 = acc[i][j][2 * h] + bias[nn], z1 = acc[i][j][2 * h + 1] + bias[nn + 1];
-                    *reinterpret_cast<__nv_bfloat162 *>(sH + r * FZ_LDH + nn) =
-                        __floats2bfloat162_rn(silu(z0), silu(z1));
-                }
+// SiLU as z (1 + tanh(z / 2)) / 2 with the hardware tanh (one SFU operation instead of an
+// exponential and a reciprocal; relative error ~2^-11, under the BF16 rounding of the result)
+__device__ __forceinline__ float silu_fast(float z)
+{
+    const float hz = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
+    return fmaf(hz, t, hz);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    mlp_forward_tc(const float *__restrict__ x, const bf16 *__restrict__ pb,
+                   const float *__restrict__ p, const bf16 *__restrict__ wpack, int64_t n_rows,
+                   float *__restrict__ y, int *err)
+{
+    extern __shared__ __align__(16) unsigned char tc_raw[];
+    unsigned char *sA = reinterpret_cast<unsigned char *>(
+        ((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sB = sA + TC_A_BYTES;
+    float4 *sW1 = reinterpret_cast<float4 *>(sB + TC_B_BYTES);  // [256]
+    float *sBias = reinterpret_cast<float *>(sW1 + HID);         // [4][256]: b1..b4
+    float4 *sW5 = reinterpret_cast<float4 *>(sBias + 4 * HID);  // [256]
+    float *sB5 = reinterpret_cast<float *>(sW5 + HID);          // [4]
+    float *red = sB5 + 4;                                        // [TC_CG-1][128][4]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        ((uintptr_t)(red + (TC_CG - 1) * TC_ROWS * NOUT) + 7) & ~(uintptr_t)7);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t wbar = tc::smem_u32(&bars[0]), mbar = tc::smem_u32(&bars[1]);
+    const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
+    const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
+    if (tid == 0) {
+        tc::mbar_init(wbar, 1);
+        tc::mbar_init(mbar, 1);
+        tc::mbar_fence_init();
     }
+    for (int n = tid; n < HID; n += TC_THREADS) {
+        sW1[n] = make_float4(bfv(pb, OFF_W1 + 0 * HID + n), bfv(pb, OFF_W1 + 1 * HID + n),
+                             bfv(pb, OFF_W1 + 2 * HID + n), bfv(pb, OFF_W1 + 3 * HID + n));
+        sBias[n] = p[OFF_B1 + n];
+        for (int l = 2; l <= 4; ++l) sBias[(l - 1) * HID + n] = p[off_b(l) + n];
+        sW5[n] = make_float4(bfv(pb, OFF_W5 + n * NOUT + 0), bfv(pb, OFF_W5 + n * NOUT + 1),
+                             bfv(pb, OFF_W5 + n * NOUT + 2), bfv(pb, OFF_W5 + n * NOUT + 3));
+    }
+    if (tid < NOUT) sB5[tid] = p[OFF_B5 + tid];
+    if (warp == 0) tc::tmem_alloc(tslot, TC_TMEM_COLS);
+    tc::fence_before_sync();
     __syncthreads();
-    // layer 5: one (row, output) dot product per thread
-    {
-        const int r = tid >> 2, o = tid & 3;
-        const int64_t gr = row0 + r;
-        float v = p[OFF_B5 + o];
-        for (int nn = 0; nn < HID; ++nn)
-            v += __bfloat162float(sH[r * FZ_LDH + nn]) * bfv(pb, OFF_W5 + nn * NOUT + o);
-        if (gr < n_rows) y[gr * NOUT + o] = v;
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // K-chunk c (k = 64 c .. 64 c + 63, all 256 n) of layer l's packed weights into sB: the
+    // B operand's K-major layout keeps each chunk's core matrices at a fixed column range of
+    // every row group, so a chunk is 32 row groups x 8 core matrices; the packed image stores
+    // the chunks one after the other (pack_hidden_weights), one bulk copy each.
+    // weights of layer l into sB (thread 0): one 128 KB image, four bulk copies
+    auto load_weights = [&](int l) {
+        tc::mbar_expect_tx(wbar, TC_B_BYTES);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            tc::bulk_g2s(b_base + c * (TC_B_BYTES / 4),
+                         wpack + (size_t)(l - 2) * HID * HID + c * (HID * HID / 4),
+                         TC_B_BYTES / 4, wbar);
+    };
+    uint32_t wphase = 0, mphase = 0;
+    bool w_pending = false, m_pending = false, failed = false;
+    if (tid == 0 && blockIdx.x < n_tiles) {
+        load_weights(2);
+        w_pending = true;
     }
+    const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, HID);
+    const int row = tid & (TC_ROWS - 1), cg1 = tid >> 7;  // layer 1: row, column group
+    const int lg = warp & 3, cg = warp >> 2;               // epilogue: TMEM lanes, column group
+    const int r = 32 * lg + lane;                          // epilogue row
+
+    auto load_x = [&](int64_t tile) {
+        const int64_t gr = tile * TC_ROWS + row;
+        return (tile < n_tiles && gr < n_rows) ? *reinterpret_cast<const float4 *>(x + gr * NIN)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float4 x_next = load_x(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
+        // ---- layer 1: row `row`, columns cg1 * 64 .. +63 ------------------------------------
+        {
+            const float4 xi = x_next;
+            x_next = load_x(tile + gridDim.x);  // in flight through this tile's layers
+#pragma unroll 2
+            for (int c = 0; c < TC_COLS / 8; ++c) {
+                const int n0 = cg1 * TC_COLS + c * 8;
+                float h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 w = sW1[n0 + j];
+                    h[j] = silu_fast(sBias[n0 + j] + xi.x * w.x + xi.y * w.y + xi.z * w.z +
+                                     xi.w * w.w);
+                }
+                *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(row, n0, HID)) =
+                    make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                               pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+            }
+        }
+        tc::fence_proxy_async();
+        float acc5[NOUT] = {0.f, 0.f, 0.f, 0.f};
+        for (int l = 2; l <= 4; ++l) {
+            // A tile written and previous accumulator reads done; weights present
+            bool to = false;
+            if (tid == 0 && w_pending) {
+                to = !tc::mbar_wait(wbar, wphase, TC_WAIT);
+                if (!to) {
+                    wphase ^= 1u;
+                    w_pending = false;
+                }
+            }
+            tc::fence_before_sync();
+            if (__syncthreads_or(to)) {
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+            if (tid == 0) {
+#pragma unroll 1
+                for (int j = 0; j < HID / 16; ++j) {
+                    const uint64_t ad = tc::smem_desc(a_base + j * 256, 128, (HID / 8) * 128);
+                    const uint64_t bd = tc::smem_desc(b_base + j * 256, 128, (HID / 8) * 128);
+                    tc::mma_bf16(tmem, ad, bd, idesc, j > 0 ? 1u : 0u);
+                }
+                tc::mma_commit(mbar);
+                m_pending = true;
+            }
+            // accumulator complete: A and B free again (thread 0 polls, the rest sleep in the
+            // block barrier instead of spinning on the mbarrier)
+            if (tid == 0) {
+                to = !tc::mbar_wait(mbar, mphase, TC_WAIT);
+                if (!to) {
+                    mphase ^= 1u;
+                    m_pending = false;
+                }
+            }
+            if (__syncthreads_or(to)) {
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+            if (tid == 0) {  // next weights while the epilogue runs
+                if (l < 4) {
+                    load_weights(l + 1);
+                    w_pending = true;
+                } else if (tile + gridDim.x < n_tiles) {
+                    load_weights(2);
+                    w_pending = true;
+                }
+            }
+            // ---- epilogue: row r (TMEM lane), columns cg * 64 .. +63 ----------------------
+            const float *bias = sBias + (l - 1) * HID;
+            const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
+#pragma unroll 1
+            for (int c = 0; c < TC_COLS / 16; c += 2) {
+                const int n0 = cg * TC_COLS + c * 16;
+                uint32_t v[2][16];
+                tc::tmem_ld16(trow + n0, v[0]);
+                tc::tmem_ld16(trow + n0 + 16, v[1]);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int nb = n0 + 16 * u;
+                    float h[16];
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        const float4 b4 = *reinterpret_cast<const float4 *>(bias + nb + 4 * j4);
+                        h[4 * j4 + 0] = silu_fast(__uint_as_float(v[u][4 * j4 + 0]) + b4.x);
+                        h[4 * j4 + 1] = silu_fast(__uint_as_float(v[u][4 * j4 + 1]) + b4.y);
+                        h[4 * j4 + 2] = silu_fast(__uint_as_float(v[u][4 * j4 + 2]) + b4.z);
+                        h[4 * j4 + 3] = silu_fast(__uint_as_float(v[u][4 * j4 + 3]) + b4.w);
+                    }
+                    if (l < 4) {
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+                            *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(r, nb + 8 * q, HID)) =
+                                make_uint4(pack_bf16x2(h[8 * q + 0], h[8 * q + 1]),
+                                           pack_bf16x2(h[8 * q + 2], h[8 * q + 3]),
+                                           pack_bf16x2(h[8 * q + 4], h[8 * q + 5]),
+                                           pack_bf16x2(h[8 * q + 6], h[8 * q + 7]));
+                    } else {  // layer 5 (256 -> 4) on the BF16-rounded activations
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float hb = __bfloat162float(__float2bfloat16_rn(h[j]));
+                            const float4 w = sW5[nb + j];
+                            acc5[0] += hb * w.x;
+                            acc5[1] += hb * w.y;
+                            acc5[2] += hb * w.z;
+                            acc5[3] += hb * w.w;
+                        }
+                    }
+                }
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+        }
+        if (failed) break;
+        // ---- layer 5: combine the column groups of each row ---------------------------------
+        if (cg > 0) {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) red[((cg - 1) * TC_ROWS + r) * NOUT + o] = acc5[o];
+        }
+        __syncthreads();
+        if (cg == 0) {
+            const int64_t gr = tile * TC_ROWS + r;
+            if (gr < n_rows) {
+                float out[NOUT];
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    out[o] = acc5[o] + sB5[o];
+#pragma unroll
+                    for (int g = 0; g < TC_CG - 1; ++g) out[o] += red[(g * TC_ROWS + r) * NOUT + o];
+                }
+                *reinterpret_cast<float4 *>(y + gr * NOUT) = make_float4(out[0], out[1], out[2], out[3]);
+            }
+        }
+    }
+    // ---- teardown: nothing of ours in flight, then free the tensor memory -------------------
+    if (tid == 0) {
+        if (failed) atomicExch(err, 1);
+        // bounded waits for our own MMAs and copies still in flight
+        if (m_pending) tc::mbar_wait(mbar, mphase, TC_WAIT);
+        if (w_pending) tc::mbar_wait(wbar, wphase, TC_WAIT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
 template <bool A_T, bool B_T, int EPI>
@@ -590,7 +759,7 @@ void free_mlp(odx_mlp *m)
                     (void *)m->dZ, (void *)m->dZ2, (void *)m->Y, (void *)m->dY, (void *)m->loss,
                     (void *)m->xin, (void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays,
                     (void *)m->fb_pix, (void *)m->fb_count, (void *)m->bcrit,
-                    (void *)m->scene_tab})
+                    (void *)m->scene_tab, (void *)m->wpack, (void *)m->tc_err})
         if (q) cudaFree(q);
     for (int l = 1; l <= 4; ++l) {
         if (m->Z[l]) cudaFree(m->Z[l]);
@@ -600,6 +769,27 @@ void free_mlp(odx_mlp *m)
 }
 
 int64_t round128(int64_t n) { return (n + 127) / 128 * 128; }
+
+// Report and clear the inference kernel's time-out flag (synchronous).
+int32_t take_tc_flag(odx_mlp *m)
+{
+    int h = 0;
+    if (cudaMemcpy(&h, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ODX_ERR_CUDA;
+    if (h == 0) return ODX_OK;
+    if (cudaMemset(m->tc_err, 0, sizeof(int)) != cudaSuccess) return ODX_ERR_CUDA;
+    return ODX_ERR_DEVICE_FLAG;
+}
+
+// Inference of n rows on the tensor cores (weights packed from the current BF16 copy).
+void infer_tc(odx_mlp *m, const float *x, int64_t n, float *y, cudaStream_t st)
+{
+    if (n <= 0) return;
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack);
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, std::max(1, m->num_sms));
+    mlp_forward_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(x, m->pb, m->p, m->wpack, n, y, m->tc_err);
+}
 
 }  // namespace
 
@@ -629,7 +819,9 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
               cudaMalloc(&m->xin, m->max_batch * NIN * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->bcrit, (BCRIT_N + 1) * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->scene_tab, sizeof(DevScene)) == cudaSuccess &&
-              cudaMalloc(&m->fb_count, sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc(&m->fb_count, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&m->wpack, (size_t)3 * HID * HID * sizeof(bf16)) == cudaSuccess &&
+              cudaMalloc(&m->tc_err, sizeof(int)) == cudaSuccess;
     for (int l = 1; l <= 4 && ok; ++l)
         ok = cudaMalloc(&m->Z[l], act) == cudaSuccess && cudaMalloc(&m->H[l], act) == cudaSuccess;
     if (!ok) {
@@ -638,8 +830,11 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
     }
     cudaMemset(m->m1, 0, NPARAM * sizeof(float));
     cudaMemset(m->m2, 0, NPARAM * sizeof(float));
-    if (cudaFuncSetAttribute(mlp_fused_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)FZ_SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TC_SMEM) != cudaSuccess ||
+        cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) !=
+            cudaSuccess ||
+        cudaMemset(m->tc_err, 0, sizeof(int)) != cudaSuccess) {
         free_mlp(m);
         return ODX_ERR_CUDA;
     }
@@ -663,7 +858,7 @@ int32_t odx_mlp_get_params(odx_mlp *m, float *host)
     if (!m || !host) return ODX_ERR_INVALID_ARG;
     MLP_CUDA(cudaSetDevice(m->device));
     MLP_CUDA(cudaMemcpy(host, m->p, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
-    return ODX_OK;
+    return take_tc_flag(m);
 }
 
 int32_t odx_mlp_set_params(odx_mlp *m, const float *host)
@@ -682,15 +877,10 @@ int32_t odx_mlp_set_params(odx_mlp *m, const float *host)
 int32_t odx_mlp_forward(odx_mlp *m, const float *x, int64_t n, float *y, void *stream)
 {
     if (!m || n < 0 || (n > 0 && (!x || !y))) return ODX_ERR_INVALID_ARG;
+    if (((uintptr_t)x & 15u) || ((uintptr_t)y & 15u)) return ODX_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CUDA(cudaSetDevice(m->device));
-    for (int64_t b0 = 0; b0 < n; b0 += m->max_batch) {
-        const int64_t nb = std::min<int64_t>(m->max_batch, n - b0);
-        const int64_t B = round128(nb);
-        (void)B;
-        mlp_fused_forward<<<blocks_for(nb, FZ_ROWS), FZ_THREADS, FZ_SMEM, st>>>(
-            x + b0 * NIN, m->pb, m->p, nb, y + b0 * NOUT);
-    }
+    infer_tc(m, x, n, y, st);
     MLP_CUDA(cudaGetLastError());
     return ODX_OK;
 }
@@ -778,14 +968,15 @@ int32_t odx_surrogate_render(odx_mlp *m, const odx_scene *scene, double band, do
     bcrit_table<<<blocks_for(BCRIT_N, 128), 128, 0, st>>>(scene->a, scene->theta_obs, scene->r_in,
                                                           m->bcrit);
     surrogate_inputs<<<blocks_for(n_pad, 256), 256, 0, st>>>(m->scene_tab, n_pad, m->surr_x);
-    mlp_fused_forward<<<blocks_for(n_pad, FZ_ROWS), FZ_THREADS, FZ_SMEM, st>>>(
-        m->surr_x, m->pb, m->p, n_pad, m->surr_y);
+    infer_tc(m, m->surr_x, n_pad, m->surr_y, st);
     surrogate_classify<<<blocks_for(n, 256), 256, 0, st>>>(m->scene_tab, m->surr_y, m->bcrit, band,
                                                           (float)p_lo, (float)p_hi, image,
                                                           m->fb_rays, m->fb_pix, m->fb_count);
     unsigned long long nfb = 0;
     MLP_CUDA(cudaMemcpyAsync(&nfb, m->fb_count, sizeof(nfb), cudaMemcpyDeviceToHost, st));
     MLP_CUDA(cudaStreamSynchronize(st));
+    const int32_t flag = take_tc_flag(m);
+    if (flag != ODX_OK) return flag;
     if (n_fallback) *n_fallback = (int64_t)nfb;
     if (nfb > 0) {
         // trace the fallback pixels (list mode, the scene's own precision) and scatter them
