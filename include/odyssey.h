@@ -199,6 +199,24 @@ int32_t odx_get_stats(odx_ctx *ctx, void *stream, odx_stats *out, int32_t reset)
  * stream, reported by odx_get_stats) when on != 0; off by default.  Not during capture. */
 int32_t odx_set_kernel_timing(odx_ctx *ctx, int32_t on);
 
+/*
+ * Spectra and light curves (Section 4.4: the light curve integrates the intensity over the
+ * frequency bins of each image).  For the scene table of an odx_render call and the image
+ * it wrote (image_dev, same layout: per scene [planes][n_beta][n_alpha], planes = n_freq
+ * for the torus, else 1):
+ *   flux_dev[k * planes + j] = sum over the pixels of scene k of I_j * dalpha * dbeta / r_obs^2,
+ *     the flux density at the observer (intensity times steradian; dalpha = (alpha_max -
+ *     alpha_min) / n_alpha, likewise dbeta), one entry per scene and plane;
+ *   lum_dev[k] (if non-NULL) = trapezoid rule of F over the scene's frequencies (torus with
+ *     n_freq >= 2), else the single plane's F.
+ * Fixed-order reduction: results do not depend on the launch schedule.  Device pointers,
+ * caller-owned, 8-byte aligned; asynchronous on `stream`; the context keeps a small scratch
+ * buffer (plane table and chunk sums).  Scenes as for odx_render (same emitter and n_freq).
+ */
+int32_t odx_image_flux(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
+                       const double *image_dev, double *flux_dev, double *lum_dev,
+                       void *stream);
+
 /* Wait for `stream` with a deadline; ODX_ERR_TIMEOUT if it has not finished in timeout_s
  * seconds (the work keeps running), ODX_ERR_DEVICE_FLAG if a kernel raised its flag. */
 int32_t odx_sync(odx_ctx *ctx, void *stream, double timeout_s);

@@ -93,6 +93,7 @@ _SIGNATURES = [
     ("odx_render_host", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P, _P]),
     ("odx_get_stats", C.c_int32, [_P, _P, C.POINTER(odx_stats), C.c_int32]),
     ("odx_sync", C.c_int32, [_P, _P, C.c_double]),
+    ("odx_image_flux", C.c_int32, [_P, C.POINTER(odx_scene), C.c_int32, _P, _P, _P, _P]),
     ("odx_set_kernel_timing", C.c_int32, [_P, C.c_int32]),
     ("odx_torus_norm", C.c_double, [C.c_double] * 6),
     ("odx_fma_peak", C.c_int32, [_P, C.c_int32, C.POINTER(C.c_double)]),
@@ -212,6 +213,13 @@ def odx_get_stats(ctx, stream: int | None = None, reset: bool = False) -> dict:
     s = odx_stats()
     _check(ctx, lib().odx_get_stats(ctx, stream or None, C.byref(s), int(reset)), "odx_get_stats")
     return {f: getattr(s, f) for f, _ in odx_stats._fields_}
+
+
+def odx_image_flux(ctx, scenes, image_ptr: int, flux_ptr: int, lum_ptr: int | None = None,
+                   stream: int | None = None) -> None:
+    arr = scene_array(scenes)
+    _check(ctx, lib().odx_image_flux(ctx, arr, len(arr), image_ptr, flux_ptr, lum_ptr or None,
+                                     stream or None), "odx_image_flux")
 
 
 def odx_set_kernel_timing(ctx, on: bool) -> None:

@@ -33,6 +33,10 @@ struct odx_ctx {
     void *hbuf = nullptr;
     size_t hbuf_bytes = 0;
     std::string last_error;
+    // scratch of odx_image_flux: plane table + chunk sums
+    void *flux_buf = nullptr;
+    size_t flux_bytes = 0;
+    std::vector<unsigned char> host_planes;
     // optional per-launch timing of the tracing kernel
     bool time_kernels = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -425,6 +429,7 @@ int32_t odx_destroy(odx_ctx *ctx)
     if (ctx->stats) cudaFree(ctx->stats);
     if (ctx->scenes) cudaFree(ctx->scenes);
     if (ctx->hbuf) cudaFree(ctx->hbuf);
+    if (ctx->flux_buf) cudaFree(ctx->flux_buf);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
     for (auto &pr : ctx->events) {
         cudaEventDestroy(pr.first);
@@ -548,6 +553,67 @@ int32_t odx_set_kernel_timing(odx_ctx *ctx, int32_t on)
     if (!ctx) return ODX_ERR_INVALID_ARG;
     ctx->time_kernels = on != 0;
     ctx->events_used = 0;
+    return ODX_OK;
+}
+
+int32_t odx_image_flux(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
+                       const double *image, double *flux, double *lum, void *stream)
+{
+    if (!ctx) return ODX_ERR_INVALID_ARG;
+    if (!image || !flux) return fail(ctx, ODX_ERR_INVALID_ARG, "image and flux must be non-NULL");
+    if (((uintptr_t)image & 7u) || ((uintptr_t)flux & 7u) || ((uintptr_t)lum & 7u))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "image, flux and lum must be 8-byte aligned");
+    int32_t rc = odx::validate_scene_table(scenes, n_scenes);
+    if (rc != ODX_OK) return fail(ctx, rc, "invalid scene table");
+    const bool torus = scenes[0].emitter == ODX_EMIT_TORUS;
+    const int32_t planes = torus ? scenes[0].n_freq : 1;
+    for (int k = 1; k < n_scenes; ++k)
+        if (scenes[k].emitter != scenes[0].emitter ||
+            (torus && scenes[k].n_freq != scenes[0].n_freq))
+            return fail(ctx, ODX_ERR_INVALID_ARG,
+                        "scene %d: all scenes of one call must share emitter and n_freq", k);
+    rc = set_device(ctx);
+    if (rc != ODX_OK) return rc;
+    rc = ensure_scene_capacity(ctx, n_scenes);
+    if (rc != ODX_OK) return rc;
+    // scene table and plane table (the image layout of odx_render)
+    ctx->host_scenes.resize(n_scenes);
+    const size_t pr = odx::plane_ref_bytes();
+    const int32_t n_planes = n_scenes * planes;
+    ctx->host_planes.resize((size_t)n_planes * pr);
+    int64_t ray = 0, img = 0, max_plane = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        const int64_t nk = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
+        odx::fill_dev_scene(ctx->host_scenes[k], scenes[k], ray, nk, img);
+        for (int j = 0; j < planes; ++j)
+            odx::fill_plane_ref(ctx->host_planes.data() + (size_t)(k * planes + j) * pr,
+                                img + (int64_t)j * nk, nk, k, j);
+        max_plane = nk > max_plane ? nk : max_plane;
+        ray += nk;
+        img += planes * nk;
+    }
+    // chunks per plane from the sizes alone (the reduction tree does not depend on the GPU)
+    int64_t ch = (max_plane + 4095) / 4096;
+    const int32_t chunks = (int32_t)(ch < 1 ? 1 : (ch > 256 ? 256 : ch));
+    const size_t need = ((ctx->host_planes.size() + 255) / 256) * 256 +
+                        (size_t)n_planes * chunks * sizeof(double);
+    if (need > ctx->flux_bytes) {
+        if (ctx->flux_buf) cudaFree(ctx->flux_buf);
+        ctx->flux_buf = nullptr;
+        ctx->flux_bytes = 0;
+        ODX_CUDA(ctx, cudaMalloc(&ctx->flux_buf, need));
+        ctx->flux_bytes = need;
+    }
+    unsigned char *base = static_cast<unsigned char *>(ctx->flux_buf);
+    double *partial = reinterpret_cast<double *>(base + ((ctx->host_planes.size() + 255) / 256) * 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    ODX_CUDA(ctx, cudaMemcpyAsync(ctx->scenes, ctx->host_scenes.data(), n_scenes * sizeof(DevScene),
+                                  cudaMemcpyHostToDevice, st));
+    ODX_CUDA(ctx, cudaMemcpyAsync(base, ctx->host_planes.data(), ctx->host_planes.size(),
+                                  cudaMemcpyHostToDevice, st));
+    const cudaError_t e = odx::launch_image_flux(ctx->scenes, base, n_scenes, planes, max_plane,
+                                                 image, partial, chunks, flux, lum, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "image flux launch");
     return ODX_OK;
 }
 

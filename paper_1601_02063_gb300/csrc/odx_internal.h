@@ -78,6 +78,14 @@ cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const od
                                int32_t num_sms, cudaStream_t st, cudaEvent_t ev0 = nullptr,
                                cudaEvent_t ev1 = nullptr);
 
+// Image-integrated flux (spectra) and its frequency integral (light curves): spectra.cu.
+cudaError_t launch_image_flux(const DevScene *scenes_dev, const void *planes_dev,
+                              int32_t n_scenes, int32_t planes_per_scene, int64_t max_plane,
+                              const double *image, double *partial, int32_t chunks,
+                              double *flux, double *lum, cudaStream_t st);
+size_t plane_ref_bytes();
+void fill_plane_ref(void *dst, int64_t first, int64_t n, int32_t scene, int32_t j);
+
 // FMA-chain peak microbenchmark: returns flop/s via *flops (synchronous).
 cudaError_t run_fma_peak(int32_t precision, int32_t num_sms, double *flops);
 
