@@ -197,7 +197,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "image": "512x512", "a": 0.94, "inclination_deg": 30,
                    "n_freq": 3, "sample": info["sample"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"],
@@ -214,13 +214,17 @@ def run_ours(args):
     world, rank, local = dist_env()
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # gloo carries the one timing aggregate (CPU tensors); the data path has no collective
+        dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     from paper_1601_02063_gb300 import binding as B
     from paper_1601_02063_gb300 import build as cuda_build
+    from paper_1601_02063_gb300 import shard
 
     cuda_build.build()
-    scene = bench_scene(args.precision, args.size)
+    full_scene = bench_scene(args.precision, args.size)
+    # weak scaling: every rank renders the image; --split: one image in row slabs
+    scene = shard.row_shard(full_scene, rank, world) if args.split else full_scene
     tr = B.Tracer(local)
     n = B.n_rays(scene)
     rec, img = tr.alloc(n, B.n_image(scene))
@@ -257,15 +261,8 @@ def run_ours(args):
     kernel_ms = st["trace_ms"] / max(1, st["trace_launches"])
     total_ms = sum(times)
     steps_local = st["steps_accepted"] + st["steps_rejected"]
-    t = torch.tensor([total_ms, float(steps_local), float(st["rays"])], dtype=torch.float64,
-                     device=f"cuda:{local}")
-    if world > 1:
-        import torch.distributed as dist
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:3], op=dist.ReduceOp.SUM)
-        t[0] = tmax[0]
-    total_ms, steps_all, rays_all = float(t[0]), float(t[1]), float(t[2])
+    import torch.distributed as dist
+    total_ms, steps_all, rays_all = shard.aggregate(total_ms, steps_local, st["rays"], dist)
     value = total_ms * 1e6 / steps_all
     ms_per_step = total_ms / args.steps
 
@@ -530,7 +527,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD if args.size == 512 else f"torus{args.size}",
@@ -582,6 +579,9 @@ def main():
     ap.add_argument("--size", type=int, default=512,
                     help="image side (the workload is 512; smaller sizes are for profiling)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--split", action="store_true",
+                    help="N > 1: split one image into row slabs (strong scaling) instead of "
+                         "one image per rank (weak scaling)")
     ap.add_argument("--no-sweep", dest="sweep", action="store_false",
                     help="omit the 64-scene batched sweep measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",

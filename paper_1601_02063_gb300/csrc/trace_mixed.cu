@@ -120,8 +120,7 @@ struct RayM {
     float yh[6];       // state high words: r, theta, phi, t, p_r, p_theta
     float th[NF + 1];  // tau high words
     float hf, hsf;     // FP32 step and error-scale step
-    float Lh, af, sgnf, r_switch, r_isco;
-    int32_t scene, mode, n_acc, n_rej;
+    float Lh, af, sgnf, r_isco;
 };
 
 // Per-lane state touched once per accepted step or less: shared memory, laid out
@@ -137,6 +136,8 @@ struct ColdM {
     float rc[kMixedBlock], pc[kMixedBlock];  // first crossing r, phi
     float Qh[kMixedBlock], Ql[kMixedBlock];  // initial Carter constant
     float Ch[kMixedBlock], Cl[kMixedBlock];  // a^2 - a L as a pair
+    float hsf[kMixedBlock], r_switch[kMixedBlock];  // error-scale step, FP64 region
+    int32_t mode[kMixedBlock], n_acc[kMixedBlock], n_rej[kMixedBlock], scene[kMixedBlock];
     float k1[6][kMixedBlock];                 // first stage of the current attempt
     long long id[kMixedBlock];
     int32_t n_cross[kMixedBlock], n64[kMixedBlock];
@@ -150,8 +151,8 @@ __device__ __forceinline__ void write_slot(const TraceArgs &A, const DevScene &S
     const long long id = C.id[t];
     MixedOut o;
     o.status = status;
-    o.n_acc = R.n_acc;
-    o.n_rej = R.n_rej;
+    o.n_acc = C.n_acc[t];
+    o.n_rej = C.n_rej[t];
     o.n_cross = C.n_cross[t];
     o.rc = C.rc[t];
     o.pc = C.pc[t];
@@ -476,10 +477,10 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     const int t = threadIdx.x;
     constexpr int NG = 4 + NF;  // stage inputs: r, theta, p_r, p_theta, tau_k
     const Geo<float> g{R.af, R.Lh, R.sgnf};
-    if (R.mode != 0) {  // (re)enter FP32
-        if (R.mode == 1) R.hf = (float)C.hd[t];
-        R.hsf = R.hf;
-        R.mode = 0;
+    if (C.mode[t] != 0) {  // (re)enter FP32
+        if (C.mode[t] == 1) R.hf = (float)C.hd[t];
+        C.hsf[t] = R.hf;
+        C.mode[t] = 0;
     }
     const float h = R.hf;
     const float hg = R.sgnf * h;  // geodesic components: dy/ds = sgn f
@@ -586,19 +587,20 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 #undef ODX_SUMS
 
     float errmax = 0.f;
+    const float hs = C.hsf[t];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const float sc = fabsf(R.yh[i]) + fabsf(R.hsf * C.k1[i][t]) + 1e-30f;
+        const float sc = fabsf(R.yh[i]) + fabsf(hs * C.k1[i][t]) + 1e-30f;
         errmax = fmaxf(errmax, __fdividef(fabsf(hg * e[i]), sc));
     }
     errmax = __fdividef(errmax, S.f_rtol32);
     if (isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.f)) {
-        ++R.n_rej;
+        ++C.n_rej[t];
         R.hf = fmaxf(0.9f * h * __powf(errmax, -0.25f), 0.1f * h);
         return R.hf < 1e-12f ? ODX_NUMERR : ODX_RUNNING;
     }
-    ++R.n_acc;
+    ++C.n_acc[t];
     const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
 #pragma unroll
     for (int i = 0; i < 6; ++i) dy[i] = __fmul_rn(dy[i], hg);  // rounded before the two-sums
@@ -636,7 +638,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     // escape: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
     if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
-    R.hsf = R.hf;
+    C.hsf[t] = R.hf;
     return ODX_RUNNING;
 }
 
@@ -670,10 +672,10 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
 #pragma unroll
     for (int k = 0; k < NF; ++k) tau[k] = df_get(R.th[k], C.tl[k][t]);
     derivs<double, NF>(g, md, y, tau, k1, kt1, kI1);
-    if (R.mode != 1) {  // entering FP64
+    if (C.mode[t] != 1) {  // entering FP64
         C.hd[t] = (double)R.hf;
         C.hsd[t] = C.hd[t];
-        R.mode = 1;
+        C.mode[t] = 1;
     }
     ++C.n64[t];
     const double h = C.hd[t];
@@ -688,11 +690,11 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     errmax /= S.s.rtol;
     if (isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.0)) {
-        ++R.n_rej;
+        ++C.n_rej[t];
         C.hd[t] = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);
         return C.hd[t] < 1e-12 ? ODX_NUMERR : ODX_RUNNING;
     }
-    ++R.n_acc;
+    ++C.n_acc[t];
     const double h_next = (errmax > 1.89e-4) ? 0.9 * h * pow(errmax, -0.2) : 5.0 * h;
     if ((cos(y[1]) > 0.0) != (cos(y[1] + dy[1]) > 0.0)) {
         double yc[6];
@@ -755,7 +757,7 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
             const DevScene &S = A.scenes[sidx];
             const MixedInit m = load80<MixedInit>(A.records + id);
             C.id[t] = id;
-            R.scene = sidx;
+            C.scene[t] = sidx;
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
                 R.yh[state_index(i)] = m.yh[i];
@@ -767,7 +769,7 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
             C.Ll[t] = m.Ll;
             R.af = m.a;
             R.sgnf = (S.s.convention == ODX_CONV_LITERAL) ? 1.f : -1.f;
-            R.r_switch = (float)S.s.r_switch;
+            C.r_switch[t] = (float)S.s.r_switch;
             C.r_stop[t] = m.r_stop;
             C.r_in[t] = m.r_in;
             C.r_start[t] = m.yh[0];
@@ -781,11 +783,11 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
             C.rc[t] = C.pc[t] = __int_as_float(0x7fc00000);
             C.Qh[t] = m.Qh;
             C.Ql[t] = m.Ql;
-            R.n_acc = R.n_rej = 0;
+            C.n_acc[t] = C.n_rej[t] = 0;
             C.n_cross[t] = C.n64[t] = 0;
             R.hf = fminf((float)S.s.h0, S.f_hmax_frac * m.yh[0]);
-            R.hsf = R.hf;
-            R.mode = -1;
+            C.hsf[t] = R.hf;
+            C.mode[t] = -1;
             R.r_isco = m.r_isco;
             if constexpr (!SINGLE) mf = medium_f<NF>(S);
             live = true;
@@ -797,13 +799,13 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
             wstat[warp][5] += __popc(act);
         }
         // per-lane precision of this step, from the lane's own radius
-        const bool want64 = live && (R.yh[0] < R.r_switch);
+        const bool want64 = live && (R.yh[0] < C.r_switch[t]);
         const unsigned b64 = __ballot_sync(kFull, want64);
         const unsigned b32 = act & ~b64;
         const bool run64 = b64 != 0u && (__popc(b64) >= A.fp64_batch || b32 == 0u);
         const bool mine = run64 ? want64 : (live && !want64);
         if (mine) {
-            const DevScene &S = A.scenes[R.scene];
+            const DevScene &S = A.scenes[A.n_scenes == 1 ? 0 : C.scene[t]];
             int32_t status;
             if (run64) {
                 // the FP64 step works on a copy: only this rare path pays for moving the
@@ -817,12 +819,13 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
                 else
                     status = step32<NF>(S, R, C, mf);
             }
-            if (status == ODX_RUNNING && R.n_acc + R.n_rej >= S.s.max_steps) status = ODX_MAXSTEPS;
+            if (status == ODX_RUNNING && C.n_acc[t] + C.n_rej[t] >= S.s.max_steps)
+                status = ODX_MAXSTEPS;
             if (status != ODX_RUNNING) {
                 write_slot<NF>(A, S, R, C, status);
                 atomicAdd(&wstat[warp][0], 1ull);
-                atomicAdd(&wstat[warp][1], (unsigned long long)R.n_acc);
-                atomicAdd(&wstat[warp][2], (unsigned long long)R.n_rej);
+                atomicAdd(&wstat[warp][1], (unsigned long long)C.n_acc[t]);
+                atomicAdd(&wstat[warp][2], (unsigned long long)C.n_rej[t]);
                 atomicAdd(&wstat[warp][3], (unsigned long long)C.n64[t]);
                 live = false;
             }

@@ -96,3 +96,30 @@ def test_autotune_picks_a_valid_launch(tracer):
         assert np.all((st >= 1) & (st <= 3))
     finally:
         B.odx_set_launch(tracer.ctx, **saved)
+
+
+def test_row_slabs_in_one_launch_equal_the_full_image(tracer):
+    """One image split into three row slabs (the multi-GPU strong-scaling partition) and
+    rendered as three scenes of one launch: the slabs' records and image, laid end to end,
+    equal the full image's (pixel centres agree to rounding; FP64 path)."""
+    from paper_1601_02063_gb300 import shard
+    full = dict(W.torus_512("fp64"), n_alpha=40, n_beta=31)
+    slabs = [shard.row_shard(full, r, 3) for r in range(3)]
+    rec_f, img_f = tracer.render(full)
+    rec_s, img_s = tracer.render(slabs)
+    n = 40 * 31
+    a, b = _records(rec_f, n), _records(rec_s, n)
+    assert np.mean(a["status"] == b["status"]) > 0.995
+    same = (a["status"] == b["status"]) & np.isfinite(a["r_cross"]) & np.isfinite(b["r_cross"])
+    rel = np.abs(a["r_cross"][same] - b["r_cross"][same]) / np.abs(a["r_cross"][same])
+    assert np.quantile(rel, 0.99) < 1e-10, np.max(rel)
+    # image: scene-major planes [slab][freq][rows][cols] -> [freq][rows][cols]
+    fi = img_f[:3 * n].cpu().numpy().reshape(3, 31, 40)
+    parts, off = [], 0
+    for s in slabs:
+        m = s["n_beta"] * 40
+        parts.append(img_s[off:off + 3 * m].cpu().numpy().reshape(3, s["n_beta"], 40))
+        off += 3 * m
+    si = np.concatenate(parts, axis=1)
+    err = np.abs(si - fi).sum() / np.abs(fi).sum()
+    assert err < 1e-8, err
