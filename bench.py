@@ -452,7 +452,29 @@ def run_ours(args):
         ms_red = timed(reduce_only, 5)
         red_bytes = 8.0 * planes * n
         hbm = measured_peak("hbm_gbs")
+        # Novikov-Thorne disk spectra for three outer radii (Section 4.3 spectra figure):
+        # one batched launch of three 512^2 scenes, 8 frequency planes each, then F_nu
+        from paper_1601_02063_gb300 import workloads as W
+        nt_scenes = [W.nt_disk(r_out=ro, n=512, precision="mixed") for ro in (12.0, 20.0, 50.0)]
+        rec_nt, img_nt = tr.alloc(B.n_rays(nt_scenes), B.n_image(nt_scenes))
+        flux_nt = torch.empty(3 * 8, dtype=torch.float64, device=f"cuda:{local}")
+        lum_nt = torch.empty(3, dtype=torch.float64, device=f"cuda:{local}")
+
+        def nt_spectra():
+            tr.render(nt_scenes, out=(rec_nt, img_nt), stream=stream)
+            B.odx_image_flux(tr.ctx, nt_scenes, img_nt.data_ptr(), flux_nt.data_ptr(),
+                             lum_nt.data_ptr(), stream.cuda_stream)
+        nt_spectra()
+        ms_nt = timed(nt_spectra, 3)
+        nt_info = {"workload": "Novikov-Thorne disk a=0.999, i=85 deg, T0=1, r_out in "
+                               "{12, 20, 50}, 512x512 each, 8 nu in [0.02, 3], one launch",
+                   "ms_per_3_spectra": ms_nt, "nu": nt_scenes[0]["freqs"],
+                   "F_nu": {str(sc["r_out"]): flux_nt[8 * k:8 * k + 8].tolist()
+                            for k, sc in enumerate(nt_scenes)},
+                   "F_integrated": lum_nt.tolist()}
+        del rec_nt, img_nt
         spectra = {
+            "novikov_thorne": nt_info,
             "workload": "torus, 16 inclinations 5..80 deg, 256x256 each, one batched launch",
             "ms_per_light_curve": ms_lc,
             "light_curve": [{"inclination_deg": i, "F_nu": flux_lc[planes * k:planes * (k + 1)].tolist(),

@@ -52,6 +52,10 @@ extern "C" {
 #define ODX_EMIT_NONE 0      /* geodesics only: grid projection, shadows (Sections 4.1-4.2) */
 #define ODX_EMIT_THIN_DISK 1 /* opaque Keplerian equatorial disk, I = g^4 r^-q (Section 4.3) */
 #define ODX_EMIT_TORUS 2     /* analytic thermal flow, radiative transfer Eqs. 30-31         */
+#define ODX_EMIT_NT_DISK 3   /* Novikov-Thorne disk (Section 4.3): opaque like THIN_DISK; each
+                                hit emits a blackbody at T(r) = T0 (8 pi F(r) / 3)^(1/4), F the
+                                Page-Thorne flux for unit accretion rate, seen as B_nu(g T) at
+                                the n_freq observed frequencies (n_freq image planes) */
 
 /* arithmetic of the integrator */
 #define ODX_FP64 0  /* every stage in FP64                                             */
@@ -78,7 +82,7 @@ typedef struct odx_scene {
     double freqs[ODX_MAX_FREQ];     /* observed frequencies nu_obs (dimensionless)      */
     double r_in, r_out, q_emis;     /* thin disk edges (r_in <= 0: r_ISCO(a)), index q   */
     double ne_index, theta_width;   /* torus n_e = r^-ne_index exp(-cos^2 / (2 w^2))    */
-    double T0, T_index;             /* torus T_e = T0 r^-T_index                         */
+    double T0, T_index;             /* torus T_e = T0 r^-T_index; NT disk: T0 scale     */
     double C_norm;                  /* torus emissivity normalisation (odx_torus_norm)  */
     double rtol;                    /* Cash-Karp relative tolerance (FP64 stages)       */
     double h0;                      /* first step in affine parameter                  */

@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 MAX_FREQ = 8
 
 STATUS = {"running": 0, "escaped": 1, "captured": 2, "disk_hit": 3, "maxsteps": 4, "numerr": 5}
-EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3}
+EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4}
 CONVENTIONS = {"physical": 0, "literal": 1}
 
 
@@ -91,6 +91,9 @@ def lib():
         sigs = {
             "orc_horizon": (D, [D]),
             "orc_isco": (D, [D]),
+            "orc_nt_flux": (D, [D, D]),
+            "orc_circ_E": (D, [D, D]),
+            "orc_circ_L": (D, [D, D]),
             "orc_ck_tableau": (None, [P(D), P(D), P(D), P(D)]),
             "orc_pixel_center": (None, [P(Scene), I32, I32, P(D), P(D)]),
             "orc_observer_point": (None, [P(Scene), D, D, P(D)]),
@@ -225,6 +228,19 @@ def horizon(a: float) -> float:
 
 def isco(a: float) -> float:
     return lib().orc_isco(a)
+
+
+def nt_flux(a: float, r: float) -> float:
+    """8 pi F(r) / 3 of the Novikov-Thorne disk (Page-Thorne integral by quadrature)."""
+    return lib().orc_nt_flux(float(a), float(r))
+
+
+def circ_E(a: float, r: float) -> float:
+    return lib().orc_circ_E(float(a), float(r))
+
+
+def circ_L(a: float, r: float) -> float:
+    return lib().orc_circ_L(float(a), float(r))
 
 
 def disk_redshift(a: float, r: float, L: float) -> float:

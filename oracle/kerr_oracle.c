@@ -213,6 +213,82 @@ double orc_disk_redshift(double a, double r, double L)
     return 1.0 / (ut * (1.0 - Omega * L));
 }
 
+/* ---- Novikov-Thorne disk (Section 4.3) ---------------------------------------------------
+ * Circular prograde equatorial orbits (Bardeen, Press & Teukolsky 1972): specific energy E,
+ * angular momentum L and angular velocity Omega.  Page & Thorne (1974): the flux from one
+ * face for accretion rate Mdot is F = Mdot f / (4 pi r) with
+ *   f(r) = -dOmega/dr (E - Omega L)^-2  int_{r_ms}^{r} (E - Omega L) dL/dr' dr'.
+ * Here: derivatives by five-point central differences in long double, the integral by
+ * adaptive Simpson quadrature (tolerance 1e-12 of the integral); returned as
+ * 8 pi F / 3 for Mdot = 1. */
+double orc_circ_E(double a, double r)
+{
+    double rs = sqrt(r);
+    return (r * rs - 2.0 * rs + a) / (pow(r, 0.75) * sqrt(r * rs - 3.0 * rs + 2.0 * a));
+}
+
+double orc_circ_L(double a, double r)
+{
+    double rs = sqrt(r);
+    return (r * r - 2.0 * a * rs + a * a) / (pow(r, 0.75) * sqrt(r * rs - 3.0 * rs + 2.0 * a));
+}
+
+static long double circ_Omega(double a, long double r) { return 1.0L / (powl(r, 1.5L) + a); }
+
+static long double circ_Ll(double a, long double r)
+{
+    long double rs = sqrtl(r);
+    return (r * r - 2.0L * a * rs + (long double)a * a) /
+           (powl(r, 0.75L) * sqrtl(r * rs - 3.0L * rs + 2.0L * a));
+}
+
+static long double circ_El(double a, long double r)
+{
+    long double rs = sqrtl(r);
+    return (r * rs - 2.0L * rs + a) / (powl(r, 0.75L) * sqrtl(r * rs - 3.0L * rs + 2.0L * a));
+}
+
+/* five-point central difference with step 1e-4 r */
+static long double ddr(long double (*fn)(double, long double), double a, long double r)
+{
+    long double h = 1e-4L * r;
+    return (-fn(a, r + 2 * h) + 8 * fn(a, r + h) - 8 * fn(a, r - h) + fn(a, r - 2 * h)) /
+           (12 * h);
+}
+
+static long double pt_integrand(double a, long double r)
+{
+    return (circ_El(a, r) - circ_Omega(a, r) * circ_Ll(a, r)) * ddr(circ_Ll, a, r);
+}
+
+static long double simpson_rec(double a, long double lo, long double hi, long double flo,
+                               long double fmid, long double fhi, long double whole,
+                               long double tol, int depth)
+{ /* tol: absolute, halved per level (1e-12 of the whole integral at the top) */
+    long double mid = 0.5L * (lo + hi), lm = 0.5L * (lo + mid), rm = 0.5L * (mid + hi);
+    long double flm = pt_integrand(a, lm), frm = pt_integrand(a, rm);
+    long double left = (mid - lo) / 6.0L * (flo + 4.0L * flm + fmid);
+    long double right = (hi - mid) / 6.0L * (fmid + 4.0L * frm + fhi);
+    if (depth <= 0 || fabsl(left + right - whole) <= 15.0L * tol)
+        return left + right + (left + right - whole) / 15.0L;
+    return simpson_rec(a, lo, mid, flo, flm, fmid, left, 0.5L * tol, depth - 1) +
+           simpson_rec(a, mid, hi, fmid, frm, fhi, right, 0.5L * tol, depth - 1);
+}
+
+double orc_nt_flux(double a, double r)
+{
+    double rms = orc_isco(a);
+    if (!(r > rms)) return 0.0;
+    long double lo = rms, hi = r, mid = 0.5L * (lo + hi);
+    long double flo = pt_integrand(a, lo), fmid = pt_integrand(a, mid), fhi = pt_integrand(a, hi);
+    long double whole = (hi - lo) / 6.0L * (flo + 4.0L * fmid + fhi);
+    long double tol = 1e-12L * fabsl(whole) + 1e-30L;
+    long double integral = simpson_rec(a, lo, hi, flo, fmid, fhi, whole, tol, 24);
+    long double eol = circ_El(a, r) - circ_Omega(a, r) * circ_Ll(a, r);
+    long double f = -ddr(circ_Omega, a, r) / (eol * eol) * integral;
+    return (double)(2.0L * f / (3.0L * r)); /* 8 pi F / 3 with F = f / (4 pi r) */
+}
+
 /* reading: torus velocity field.  Keplerian Omega(r) at BL radius r where r >= r_ISCO
  * and the orbit is timelike at (r, theta); the zero-angular-momentum observer
  * Omega = 2 a r / A elsewhere.  u^t from u.u = -1 with the metric of Eq. 1. */
@@ -462,12 +538,23 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
                 out->r_cross = yc[0];
                 out->phi_cross = yc[2];
             }
-            if (sc->emitter == ORC_EMIT_THIN_DISK && yc[0] >= r_in && yc[0] <= sc->r_out) {
+            if ((sc->emitter == ORC_EMIT_THIN_DISK || sc->emitter == ORC_EMIT_NT_DISK) &&
+                yc[0] >= r_in && yc[0] <= sc->r_out) {
                 status = ORC_DISK_HIT;
                 out->r_hit = yc[0];
                 out->phi_hit = yc[2];
                 out->g = orc_disk_redshift(sc->a, yc[0], L);
                 out->intensity = pow(out->g, 4.0) * pow(yc[0], -sc->q_emis);
+                if (sc->emitter == ORC_EMIT_NT_DISK) {
+                    /* blackbody at T(r) seen at g T (I_nu / nu^3 invariant along the ray) */
+                    double T = sc->T0 * pow(orc_nt_flux(sc->a, yc[0]), 0.25);
+                    double gT = out->g * T;
+                    for (int k = 0; k < sc->n_freq; ++k) {
+                        double nu = sc->freqs[k];
+                        out->I_nu[k] = 2.0 * nu * nu * nu / expm1(nu / gT);
+                    }
+                    out->intensity = 2.0 * pow(3.14159265358979323846, 4.0) / 15.0 * pow(gT, 4.0);
+                }
                 memcpy(y, yc, sizeof(double) * N_GEO);
                 s += sig;
                 break;

@@ -30,6 +30,7 @@
 #define ORC_EMIT_THIN_DISK 1 /* opaque Keplerian equatorial disk, I = g^4 r^-q  */
 #define ORC_EMIT_TORUS 2     /* analytic thermal torus, RT Eqs. 30-31           */
 #define ORC_EMIT_CONST 3     /* test medium: dtau/ds = kappa, dI/ds = eps e^-tau */
+#define ORC_EMIT_NT_DISK 4   /* Novikov-Thorne disk: blackbody at T0 (8 pi F / 3)^1/4 */
 
 /* sign conventions for the traced photon (see the direction reading in the design notes) */
 #define ORC_CONV_PHYSICAL 0 /* real outgoing photon, traced back in affine time */
@@ -73,6 +74,13 @@ void orc_init_ray(const orc_scene *sc, double alpha, double beta, double y0[6], 
                   double *Q, double vin[3]);
 void orc_geodesic_rhs(double a, double L, const double y[6], double f[6]);
 double orc_disk_redshift(double a, double r, double L);
+/* Page-Thorne flux of one face of the Novikov-Thorne disk for unit accretion rate, as
+ * 8 pi F(r) / 3, by quadrature of the Page & Thorne (1974) integral; 0 inside r_ISCO. */
+double orc_nt_flux(double a, double r);
+/* Specific energy and angular momentum of prograde circular equatorial orbits (E = 1
+ * normalisation of the photon does not enter; Bardeen, Press & Teukolsky 1972). */
+double orc_circ_E(double a, double r);
+double orc_circ_L(double a, double r);
 double orc_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
                       double r_outer);
 int orc_trace_ray(const orc_scene *sc, double alpha, double beta, orc_result *out);

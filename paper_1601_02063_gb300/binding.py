@@ -20,7 +20,7 @@ MAX_FREQ = 8
  ERR_TOO_LARGE) = range(8)
 STATIC_MAX_SCENES = 64
 RUNNING, ESCAPED, CAPTURED, DISK_HIT, MAXSTEPS, NUMERR = range(6)
-EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2}
+EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "nt_disk": 3}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 CONVENTIONS = {"physical": 0, "literal": 1}
 
@@ -385,7 +385,7 @@ def n_rays(scenes) -> int:
 
 
 def image_planes(d: dict) -> int:
-    return len(d["freqs"]) if d["emitter"] == "torus" else 1
+    return len(d["freqs"]) if d["emitter"] in ("torus", "nt_disk") else 1
 
 
 def n_image(scenes) -> int:

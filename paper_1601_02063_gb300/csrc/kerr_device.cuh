@@ -114,6 +114,30 @@ __device__ __forceinline__ double disk_redshift(double a, double r, double L)
     return 1.0 / (ut * (1.0 - Om * L));
 }
 
+// Novikov-Thorne disk (Section 4.3): flux per unit proper area and time from one face of
+// the disk at Boyer-Lindquist radius r, for unit accretion rate, in the closed form of
+// Page & Thorne (1974) with x = sqrt(r), x0 = sqrt(r_ms) and the roots x1, x2, x3 of
+// x^3 - 3x + 2a = 0; returned as 8 pi F / 3, which tends to r^-3 far out.  Zero inside r_ms.
+__host__ __device__ inline double nt_flux_hat(double a, double r, double r_ms)
+{
+    if (!(r > r_ms)) return 0.0;
+    const double x = sqrt(r), x0 = sqrt(r_ms);
+    const double th = acos(a) / 3.0, third = 1.0471975511965976;  // pi / 3
+    const double x1 = 2.0 * cos(th - third), x2 = 2.0 * cos(th + third), x3 = -2.0 * cos(th);
+    double b = x - x0 - 1.5 * a * log(x / x0);
+    b -= 3.0 * (x1 - a) * (x1 - a) / (x1 * (x1 - x2) * (x1 - x3)) * log((x - x1) / (x0 - x1));
+    b -= 3.0 * (x2 - a) * (x2 - a) / (x2 * (x2 - x1) * (x2 - x3)) * log((x - x2) / (x0 - x2));
+    b -= 3.0 * (x3 - a) * (x3 - a) / (x3 * (x3 - x1) * (x3 - x2)) * log((x - x3) / (x0 - x3));
+    const double f = 1.5 * b / (x * x * (x * x * x - 3.0 * x + 2.0 * a));
+    return (2.0 / 3.0) * f / r;  // 8 pi F / 3 with F = f / (4 pi r)
+}
+
+// Planck intensity B_nu(T) = 2 nu^3 / (exp(nu / T) - 1) (h = c = k = 1), 0 for T <= 0.
+__host__ __device__ inline double planck(double nu, double T)
+{
+    return T > 0.0 ? 2.0 * nu * nu * nu / expm1(nu / T) : 0.0;
+}
+
 // Observer of one ray: spin, distance, sin and cos of theta_obs and phi_obs,
 // Ro = sqrt(r_obs^2 + a^2), and the image-plane point (alpha, beta).
 struct ObsIn {

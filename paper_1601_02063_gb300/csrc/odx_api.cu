@@ -89,17 +89,21 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
         if (s.n_alpha < 1 || s.n_beta < 1)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
     }
-    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_TORUS)
+    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_NT_DISK)
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown emitter %d", k, s.emitter);
-    if (s.emitter == ODX_EMIT_THIN_DISK &&
+    if (odx::disk_emitter(s.emitter) &&
         (!finite(s.r_in) || !finite(s.r_out) || !(s.r_out > 0.0) || !finite(s.q_emis)))
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad thin-disk parameters", k);
-    if (s.emitter == ODX_EMIT_TORUS) {
+    if (s.emitter == ODX_EMIT_NT_DISK && (!(s.T0 > 0.0) || !finite(s.T0)))
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: NT disk needs T0 > 0", k);
+    if (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK) {
         if (s.n_freq < 1 || s.n_freq > ODX_MAX_FREQ)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: n_freq must be 1..%d", k, ODX_MAX_FREQ);
         for (int f = 0; f < s.n_freq; ++f)
             if (!finite(s.freqs[f]) || !(s.freqs[f] > 0.0))
                 return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: frequencies must be > 0", k);
+    }
+    if (s.emitter == ODX_EMIT_TORUS) {
         if (!finite(s.C_norm) || s.C_norm < 0.0 || !(s.theta_width > 0.0) || !(s.T0 > 0.0) ||
             !finite(s.ne_index) || !finite(s.T_index) || !finite(s.theta_width) || !finite(s.T0))
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad torus parameters", k);
@@ -178,13 +182,13 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
         int32_t rc = validate_scene(ctx, scenes[k], k, list_mode);
         if (rc != ODX_OK) return rc;
         if (scenes[k].emitter != scenes[0].emitter || scenes[k].precision != scenes[0].precision ||
-            (scenes[0].emitter == ODX_EMIT_TORUS && scenes[k].n_freq != scenes[0].n_freq))
+            odx::scene_planes(scenes[k]) != odx::scene_planes(scenes[0]))
             return fail(ctx, ODX_ERR_INVALID_ARG,
                         "scene %d: all scenes of one call must share emitter, precision, n_freq", k);
     }
     ctx->host_scenes.resize(n_scenes);
     int64_t ray = 0, img = 0;
-    const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
+    const int64_t nf = odx::scene_planes(scenes[0]);
     for (int k = 0; k < n_scenes; ++k) {
         DevScene &d = ctx->host_scenes[k];
         const int64_t nk = list_mode ? n_list : (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
@@ -349,7 +353,7 @@ int32_t validate_scene_table(const odx_scene *scenes, int32_t n_scenes)
         const int32_t rc = validate_scene(nullptr, scenes[k], k, false);
         if (rc != ODX_OK) return rc;
         if (scenes[k].emitter != scenes[0].emitter || scenes[k].precision != scenes[0].precision ||
-            (scenes[0].emitter == ODX_EMIT_TORUS && scenes[k].n_freq != scenes[0].n_freq))
+            odx::scene_planes(scenes[k]) != odx::scene_planes(scenes[0]))
             return ODX_ERR_INVALID_ARG;
     }
     return ODX_OK;
@@ -489,7 +493,7 @@ int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
         const int64_t p = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
         nr += p;
-        ni += p * (scenes[k].emitter == ODX_EMIT_TORUS ? scenes[k].n_freq : 1);
+        ni += p * odx::scene_planes(scenes[k]);
     }
     const size_t rec_bytes = (size_t)nr * sizeof(odx_ray_record);
     const size_t img_bytes = (size_t)ni * sizeof(double);
@@ -565,11 +569,9 @@ int32_t odx_image_flux(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
         return fail(ctx, ODX_ERR_INVALID_ARG, "image, flux and lum must be 8-byte aligned");
     int32_t rc = odx::validate_scene_table(scenes, n_scenes);
     if (rc != ODX_OK) return fail(ctx, rc, "invalid scene table");
-    const bool torus = scenes[0].emitter == ODX_EMIT_TORUS;
-    const int32_t planes = torus ? scenes[0].n_freq : 1;
+    const int32_t planes = odx::scene_planes(scenes[0]);
     for (int k = 1; k < n_scenes; ++k)
-        if (scenes[k].emitter != scenes[0].emitter ||
-            (torus && scenes[k].n_freq != scenes[0].n_freq))
+        if (scenes[k].emitter != scenes[0].emitter || odx::scene_planes(scenes[k]) != planes)
             return fail(ctx, ODX_ERR_INVALID_ARG,
                         "scene %d: all scenes of one call must share emitter and n_freq", k);
     rc = set_device(ctx);
@@ -679,7 +681,7 @@ int32_t odx_graph_create(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes
     rc = set_device(ctx);
     if (rc != ODX_OK) return rc;
     std::vector<DevScene> table(n_scenes);
-    const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
+    const int64_t nf = odx::scene_planes(scenes[0]);
     int64_t ray = 0, img = 0;
     for (int k = 0; k < n_scenes; ++k) {
         const int64_t nk = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
@@ -745,7 +747,7 @@ int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, vo
     for (int k = 0; k < n_scenes; ++k) {
         const int64_t p = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;
         nr += p;
-        ni += p * (scenes[k].emitter == ODX_EMIT_TORUS ? scenes[k].n_freq : 1);
+        ni += p * odx::scene_planes(scenes[k]);
     }
     const bool mixed = scenes[0].precision == ODX_MIXED;
     std::vector<odx_launch> cands;

@@ -9,6 +9,18 @@
 
 namespace odx {
 
+// Image planes of a scene: one per observed frequency for the torus and the Novikov-Thorne
+// disk, otherwise one (thin-disk intensity, or zero for geodesics only).
+__host__ __device__ inline int32_t scene_planes(const odx_scene &s)
+{
+    return (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK) ? s.n_freq : 1;
+}
+// Emitters whose rays stop on the opaque equatorial disk r_in <= r <= r_out.
+__host__ __device__ inline bool disk_emitter(int32_t e)
+{
+    return e == ODX_EMIT_THIN_DISK || e == ODX_EMIT_NT_DISK;
+}
+
 // A scene as the kernels read it: the caller's description plus where its rays sit in the
 // launch-wide ray numbering and where its image planes start.
 struct DevScene {

@@ -84,7 +84,7 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
 
     // scene table built on the host stack (no heap, no device allocation)
     DevScene table[ODX_STATIC_MAX_SCENES];
-    const int64_t nf = scenes[0].emitter == ODX_EMIT_TORUS ? scenes[0].n_freq : 1;
+    const int64_t nf = odx::scene_planes(scenes[0]);
     int64_t ray = 0, img = 0;
     for (int k = 0; k < n_scenes; ++k) {
         const int64_t nk = (int64_t)scenes[k].n_alpha * scenes[k].n_beta;

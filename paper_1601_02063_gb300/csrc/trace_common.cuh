@@ -113,6 +113,19 @@ __device__ __forceinline__ double ray_r_isco(const TraceArgs &A, const DevScene 
     return A.list_mode ? isco_radius(a) : S.o_r_isco;
 }
 
+// Image planes of a Novikov-Thorne disk hit at (r, g): B_nu(g T(r)) at each observed
+// frequency (Liouville: I_nu / nu^3 invariant), zero for rays that miss the disk.  Returns
+// the bolometric observed intensity g^4 (2 pi^4 / 15) T^4 for the record.
+__device__ inline double nt_disk_planes(const DevScene &S, double *img, double a, double r_ms,
+                                        double r, double g, bool hit)
+{
+    const double T = hit ? S.s.T0 * sqrt(sqrt(nt_flux_hat(a, r, r_ms))) : 0.0;
+    if (img)
+        for (int k = 0; k < S.s.n_freq; ++k) img[(int64_t)k * S.n_rays] = planck(S.s.freqs[k], g * T);
+    const double gT = g * T;
+    return hit ? 12.987878804533656 * gT * gT * gT * gT : 0.0;  // 2 pi^4 / 15
+}
+
 struct RecordOut {
     int32_t status, n_acc, n_rej, n_cross;
     double r_cross, phi_cross, r_hit, phi_hit, g, intensity, H_end, Q_drift;

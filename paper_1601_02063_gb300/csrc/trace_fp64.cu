@@ -96,9 +96,12 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     o.intensity = inten;
     o.H_end = null_violation(R.a, R.L, yend);
     o.Q_drift = (carter_q(R.a, R.L, yend) - R.Q0) / fmax(fabs(R.Q0), 1.0);
+    double *img = A.image ? A.image + S.img_offset + (R.id - S.ray_begin) : nullptr;
+    if (S.s.emitter == ODX_EMIT_NT_DISK)
+        o.intensity = nt_disk_planes(S, img, R.a, ray_r_isco(A, S, R.a), r_hit, g,
+                                     status == ODX_DISK_HIT);
     store_record(A.records + R.id, o);
-    if (A.image) {
-        double *img = A.image + S.img_offset + (R.id - S.ray_begin);
+    if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
         if constexpr (NF > 0) {
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
@@ -198,8 +201,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         R.r_cross = yc[0];
                         R.phi_cross = yc[2];
                     }
-                    if (S.s.emitter == ODX_EMIT_THIN_DISK && yc[0] >= R.r_in &&
-                        yc[0] <= R.r_out) {
+                    if (disk_emitter(S.s.emitter) && yc[0] >= R.r_in && yc[0] <= R.r_out) {
                         const double gz = disk_redshift(R.a, yc[0], R.L);
                         const double g2 = gz * gz;
                         const double inten = g2 * g2 * pow(yc[0], -S.s.q_emis);

@@ -451,7 +451,7 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, Cold
         C.rc[t] = ch[0];
         C.pc[t] = ch[2];
     }
-    if (S.s.emitter == ODX_EMIT_THIN_DISK && ch[0] >= C.r_in[t] && ch[0] <= S.f_r_out) {
+    if (disk_emitter(S.s.emitter) && ch[0] >= C.r_in[t] && ch[0] <= S.f_r_out) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             R.yh[i] = ch[i];
@@ -873,9 +873,12 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
         const double g2 = r.g * r.g;
         r.intensity = g2 * g2 * pow(yend[0], -S.s.q_emis);
     }
+    double *img = A.image ? A.image + S.img_offset + (id - S.ray_begin) : nullptr;
+    if (S.s.emitter == ODX_EMIT_NT_DISK)
+        r.intensity = nt_disk_planes(S, img, a, ray_r_isco(A, S, a), r.r_hit, r.g,
+                                     o.status == ODX_DISK_HIT);
     store_record(A.records + id, r);
-    if (A.image) {
-        double *img = A.image + S.img_offset + (id - S.ray_begin);
+    if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
         if (S.s.emitter == ODX_EMIT_TORUS) {
             for (int k = 0; k < S.s.n_freq; ++k) {
                 const float2 p = *reinterpret_cast<const float2 *>(img + (int64_t)k * S.n_rays);

@@ -67,6 +67,17 @@ def torus_hard_4096(precision: str = "mixed") -> dict:
                  freqs=freqs, precision=precision)
 
 
+def nt_disk(r_out: float = 20.0, n: int = 512, precision: str = "mixed") -> dict:
+    """Novikov-Thorne disk spectrum (Section 4.3, the spectra figure): a = 0.999, i = 85 deg,
+    r_obs = 1000, disk r_ISCO .. r_out, temperature scale T0 = 1, 8 log-spaced frequencies in
+    [0.02, 3]; window [-(r_out + 2), r_out + 2]^2 at n x n."""
+    w = r_out + 2.0
+    freqs = [float(v) for v in np.geomspace(0.02, 3.0, 8)]
+    return scene(a=0.999, theta_obs=math.radians(85.0), alpha_min=-w, alpha_max=w, beta_min=-w,
+                 beta_max=w, n_alpha=n, n_beta=n, emitter="nt_disk", r_out=r_out, T0=1.0,
+                 freqs=freqs, precision=precision)
+
+
 def sweep_64(seed: int = SEED, precision: str = "mixed") -> list[dict]:
     """64 thin-disk scenes: resolution from {128,256,512,1024}^2, a ~ U[0, 0.998],
     i ~ U[5, 85] deg, disk and window as in the 64x64 thin-disk scene."""

@@ -87,3 +87,32 @@ def test_thin_disk_bolometric_flux(tracer, orc):
     ref = S.image_flux(sc, S.image_planes(sc, orc.render(sc)))
     assert abs(flux[0] - ref[0]) / ref[0] < 1e-8
     assert lum[0] == flux[0]
+
+
+def test_nt_disk_image_and_spectrum_match_oracle(tracer, orc):
+    """Novikov-Thorne disk (a = 0.999, i = 85 deg, r_out = 12): the FP64 path's 8 image planes
+    B_nu(g T) pixel by pixel and the spectrum F_nu against the oracle (Page-Thorne flux by
+    quadrature there, closed form here); the mixed path within its image tolerance."""
+    sc = W.nt_disk(r_out=12.0, n=40, precision="fp64")
+    rec, img = tracer.render(sc)
+    ref = orc.render(sc)
+    planes = S.image_planes(sc, ref)
+    n = 40 * 40
+    got = img[:8 * n].cpu().numpy().reshape(8, n)
+    from paper_1601_02063_gb300 import binding as B
+    r = B.records_to_numpy(rec)[:n]
+    hit = (r["status"] == 3) & (ref["status"] == 3)
+    assert hit.sum() > 100
+    rel = np.abs(got[:, hit] - planes[:, hit]) / np.maximum(np.abs(planes[:, hit]), 1e-300)
+    assert np.quantile(rel, 0.999) < 1e-8, np.max(rel)
+    for k in range(8):
+        assert np.abs(got[k] - planes[k]).sum() / np.abs(planes[k]).sum() < 1e-8
+    flux, lum = _flux(tracer, [sc], img)
+    F = S.image_flux(sc, planes)
+    assert np.all(np.abs(flux - F) / F < 1e-8), (flux, F)
+    assert math.isclose(lum[0], S.light_curve_point(sc, F), rel_tol=1e-8)
+    mixed = dict(sc, precision="mixed")
+    _, img_m = tracer.render(mixed)
+    gm = img_m[:8 * n].cpu().numpy().reshape(8, n)
+    for k in range(8):
+        assert np.abs(gm[k] - got[k]).sum() / np.abs(got[k]).sum() < 1e-3
