@@ -486,6 +486,31 @@ def run_ours(args):
         }
         del rec_lc, img_lc
 
+    # secondary: the paper's own timing workload (Table 1: 1024^2 grid projection at
+    # a = 0.95, i = 60 deg, FP64) through the FP64 and the mixed path, same metric as the
+    # paper's runtime / total steps
+    paper_wl = None
+    if args.size == 512:
+        from paper_1601_02063_gb300 import workloads as W
+        out_p = {}
+        for prec in ("fp64", "mixed"):
+            sc_p = W.projection_1024(prec)
+            rec_p, img_p = tr.alloc(B.n_rays(sc_p), B.n_image(sc_p))
+            tr.render(sc_p, out=(rec_p, img_p))
+            torch.cuda.synchronize()
+            tr.stats(reset=True)
+            ms_p = timed(lambda: tr.render(sc_p, out=(rec_p, img_p), stream=stream), 1)
+            st_p = tr.stats(reset=True)
+            steps_p = st_p["steps_accepted"] + st_p["steps_rejected"]
+            out_p[prec] = {"ms_per_image": ms_p, "ns_per_photon_step": ms_p * 1e6 / steps_p,
+                           "steps_per_photon": steps_p / st_p["rays"]}
+            del rec_p, img_p
+        paper_wl = {"workload": "1024x1024 grid projection, a=0.95, i=60 deg, [-15,15]^2, "
+                                "rtol 1e-8 (the paper's Table 1 workload; FOV and tolerance "
+                                "unstated there)",
+                    "paper_ns_per_photon_step": 16.31, "paper_steps_per_photon": 1505,
+                    "paper_hardware": "GeForce GTX 780 Ti, FP64", **out_p}
+
     # secondary: the 4096^2 near-edge-on hard case (a = 0.998, i = 85 deg, 8 frequencies),
     # mixed precision, with its step-count distribution; accuracy against FP64 on the same
     # scene at 512^2
@@ -567,6 +592,7 @@ def run_ours(args):
         "surrogate": surrogate,
         "hard_case": hard,
         "spectra": spectra,
+        "paper_workload": paper_wl,
         "gpu_launches": args.steps * (3 if args.precision == "mixed" else 1),
         "tracer_kernel_ms": kernel_ms,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,

@@ -67,6 +67,15 @@ def torus_hard_4096(precision: str = "mixed") -> dict:
                  freqs=freqs, precision=precision)
 
 
+def projection_1024(precision: str = "fp64") -> dict:
+    """The paper's timing workload (Section 5, Table 1): grid projection (geodesics only, the
+    first equatorial crossing recorded) at a = 0.95, i = 60 deg, r_obs = 1000, 1024x1024.
+    The paper states neither the field of view nor the tolerance; here [-15, 15]^2 and
+    rtol 1e-8 as in the other scenes."""
+    return scene(a=0.95, theta_obs=math.radians(60.0), n_alpha=1024, n_beta=1024,
+                 emitter="none", precision=precision)
+
+
 def nt_disk(r_out: float = 20.0, n: int = 512, precision: str = "mixed") -> dict:
     """Novikov-Thorne disk spectrum (Section 4.3, the spectra figure): a = 0.999, i = 85 deg,
     r_obs = 1000, disk r_ISCO .. r_out, temperature scale T0 = 1, 8 log-spaced frequencies in
