@@ -3,7 +3,7 @@
 // activations, FP32 accumulation.  Training (forward, backward, Adam) runs in the kernels
 // below, the 256 x 256 layers on the BF16 mma.sync GEMM of mlp_gemm.cuh and the 4-wide input
 // and output layers on CUDA cores; inference is one fused kernel per 128-row tile on the
-// tcgen05 tensor cores (mlp_forward_tc, accumulator in tensor memory).  The surrogate render
+// tcgen05 tensor cores (mlp_chain_tc, accumulator in tensor memory).  The surrogate render
 // classifies each pixel and hands the uncertain ones (near the Bardeen critical curve or
 // with an unsure capture probability) back to the ray tracer.
 #include <cuda_bf16.h>
@@ -63,10 +63,11 @@ struct odx_mlp {
     float *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
     int64_t step = 0;
     bf16 *Z[5] = {}, *H[5] = {};  // layers 1..4
-    bf16 *dZ = nullptr, *dZ2 = nullptr;
+    bf16 *dZ[5] = {};             // dL/dZ_l, layers 1..4 (backward)
     float *Y = nullptr, *dY = nullptr, *loss = nullptr;
     float *xin = nullptr;   // padded input rows for inference
-    bf16 *wpack = nullptr;  // hidden-layer weights in the tensor-core operand layout
+    bf16 *wpack = nullptr;   // hidden-layer weights as forward tensor-core operands (W^T)
+    bf16 *wpackB = nullptr;  // ... and as backward operands (W)
     int *tc_err = nullptr;  // set by the inference kernel if a wait timed out
     int num_sms = 0;
     // surrogate render workspace
@@ -88,22 +89,8 @@ namespace {
 
 __device__ __forceinline__ float bfv(const bf16 *p, int64_t i) { return __bfloat162float(p[i]); }
 
-// ---- layer 1 (4 -> 256) and layer 5 (256 -> 4) on CUDA cores ------------------------------
+// ---- layer 5 (256 -> 4) and the gradients of the 4-wide layers on CUDA cores ---------------
 // weights from the BF16 copy, biases from the FP32 master (added in the FP32 epilogue)
-__global__ void layer1_fwd(const float *__restrict__ x, const bf16 *__restrict__ pb,
-                           const float *__restrict__ p, int64_t B, bf16 *Z, bf16 *H)
-{
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= B * HID) return;
-    const int64_t b = idx / HID;
-    const int n = (int)(idx % HID);
-    float z = p[OFF_B1 + n];
-#pragma unroll
-    for (int k = 0; k < NIN; ++k) z += x[b * NIN + k] * bfv(pb, OFF_W1 + k * HID + n);
-    if (Z) Z[idx] = __float2bfloat16_rn(z);
-    H[idx] = __float2bfloat16_rn(silu(z));
-}
-
 // One warp per sample row: y = H4 . W5 + b5 (lane-strided dot products, warp reduction);
 // with targets: loss and dL/dy (1/B folded in).
 __global__ void layer5_fwd_loss(const bf16 *__restrict__ H4, const bf16 *__restrict__ pb,
@@ -445,16 +432,39 @@ constexpr size_t TC_RED_BYTES = (size_t)(TC_CG - 1) * TC_ROWS * NOUT * sizeof(fl
 constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_B_BYTES + TC_CONST_BYTES + TC_RED_BYTES + 64;
 static_assert(TC_SMEM <= 232448, "shared memory of one CTA");
 
-// Hidden-layer weights W_l[k][n] (FP32 master's BF16 copy) -> B operand B[n][k] in the
-// K-major core-matrix layout, one 128 KB block per layer.
-__global__ void pack_hidden_weights(const bf16 *__restrict__ pb, bf16 *__restrict__ wpack)
+// Three passes share one kernel shape (a 128-row tile through the three 256 x 256 layers):
+enum TcMode : int {
+    TC_INFER = 0,  // inference: layers 1-5, outputs y
+    TC_TRAIN = 1,  // training forward: Z_l and H_l (l = 1..4) kept in HBM for the backward pass
+    TC_BWD = 2,    // backward: dZ_4 -> dZ_3, dZ_2, dZ_1 through W_4^T, W_3^T, W_2^T and SiLU'
+};
+
+struct TcArgs {
+    const float *x;     // forward: input rows [n][4]
+    const bf16 *pb;     // BF16 parameters (W1, W5)
+    const float *p;     // FP32 parameters (biases)
+    const bf16 *wpack;  // the three packed B operands in the order of use, 128 KB each
+    int64_t n_rows;
+    float *y;           // TC_INFER: outputs [n][4]
+    bf16 *Z[5], *H[5];  // TC_TRAIN: written (l = 1..4); TC_BWD: Z_1..Z_3 read
+    const bf16 *dZ4;    // TC_BWD: input
+    bf16 *dZ[5];        // TC_BWD: dZ_3, dZ_2, dZ_1 written
+    int *err;
+};
+
+// Forward operands: B[n][k] = W_l[k][n] (z = h W); backward operands: B[k][n] = W_l[k][n]
+// (dh = dz W^T).  Either way the K-major core-matrix layout, one 128 KB block per layer,
+// blocks in the order the pass uses them (forward l = 2, 3, 4; backward l = 4, 3, 2).
+__global__ void pack_hidden_weights(const bf16 *__restrict__ pb, bf16 *__restrict__ wpack,
+                                    int backward)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 3 * HID * HID) return;
-    const int l = 2 + idx / (HID * HID), e = idx % (HID * HID);
-    const int n = e / HID, k = e % HID;
-    wpack[(size_t)(l - 2) * HID * HID + tc::kmajor_offset(n, k, HID) / 2] =
-        pb[off_w(l) + k * HID + n];
+    const int i = idx / (HID * HID), e = idx % (HID * HID);
+    const int k = e / HID, n = e % HID;  // W_l[k][n]
+    const int l = backward ? 4 - i : 2 + i;
+    const uint32_t off = backward ? tc::kmajor_offset(k, n, HID) : tc::kmajor_offset(n, k, HID);
+    wpack[(size_t)i * HID * HID + off / 2] = pb[off_w(l) + k * HID + n];
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -463,20 +473,44 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// SiLU as z (1 + tanh(z / 2)) / 2 with the hardware tanh (one SFU operation instead of an
-// exponential and a reciprocal; relative error ~2^-11, under the BF16 rounding of the result)
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(x));
+    return t;
+}
+// SiLU as z (1 + tanh(z / 2)) / 2 and its derivative s (1 + z (1 - s)), s = (1 + tanh(z/2)) / 2,
+// with the hardware tanh (one SFU operation; relative error ~2^-11, under the BF16 rounding)
 __device__ __forceinline__ float silu_fast(float z)
 {
     const float hz = 0.5f * z;
-    float t;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
-    return fmaf(hz, t, hz);
+    return fmaf(hz, tanh_fast(hz), hz);
+}
+__device__ __forceinline__ float dsilu_fast(float z)
+{
+    const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+    return s * fmaf(z, 1.f - s, 1.f);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    mlp_forward_tc(const float *__restrict__ x, const bf16 *__restrict__ pb,
-                   const float *__restrict__ p, const bf16 *__restrict__ wpack, int64_t n_rows,
-                   float *__restrict__ y, int *err)
+__device__ __forceinline__ uint4 pack8(const float *h)
+{
+    return make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                      pack_bf16x2(h[6], h[7]));
+}
+__device__ __forceinline__ void unpack8(uint4 u, float *f)
+{
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+        const float2 t = __bfloat1622float2(v);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_constant__ TcArgs A)
 {
     extern __shared__ __align__(16) unsigned char tc_raw[];
     unsigned char *sA = reinterpret_cast<unsigned char *>(
@@ -494,80 +528,101 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t wbar = tc::smem_u32(&bars[0]), mbar = tc::smem_u32(&bars[1]);
     const uint32_t a_base = tc::smem_u32(sA), b_base = tc::smem_u32(sB);
+    const int64_t n_rows = A.n_rows;
     const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
     if (tid == 0) {
         tc::mbar_init(wbar, 1);
         tc::mbar_init(mbar, 1);
         tc::mbar_fence_init();
     }
-    for (int n = tid; n < HID; n += TC_THREADS) {
-        sW1[n] = make_float4(bfv(pb, OFF_W1 + 0 * HID + n), bfv(pb, OFF_W1 + 1 * HID + n),
-                             bfv(pb, OFF_W1 + 2 * HID + n), bfv(pb, OFF_W1 + 3 * HID + n));
-        sBias[n] = p[OFF_B1 + n];
-        for (int l = 2; l <= 4; ++l) sBias[(l - 1) * HID + n] = p[off_b(l) + n];
-        sW5[n] = make_float4(bfv(pb, OFF_W5 + n * NOUT + 0), bfv(pb, OFF_W5 + n * NOUT + 1),
-                             bfv(pb, OFF_W5 + n * NOUT + 2), bfv(pb, OFF_W5 + n * NOUT + 3));
+    if constexpr (MODE != TC_BWD) {
+        for (int n = tid; n < HID; n += TC_THREADS) {
+            sW1[n] = make_float4(bfv(A.pb, OFF_W1 + 0 * HID + n), bfv(A.pb, OFF_W1 + 1 * HID + n),
+                                 bfv(A.pb, OFF_W1 + 2 * HID + n), bfv(A.pb, OFF_W1 + 3 * HID + n));
+            sBias[n] = A.p[OFF_B1 + n];
+            for (int l = 2; l <= 4; ++l) sBias[(l - 1) * HID + n] = A.p[off_b(l) + n];
+            sW5[n] = make_float4(bfv(A.pb, OFF_W5 + n * NOUT + 0), bfv(A.pb, OFF_W5 + n * NOUT + 1),
+                                 bfv(A.pb, OFF_W5 + n * NOUT + 2), bfv(A.pb, OFF_W5 + n * NOUT + 3));
+        }
+        if (tid < NOUT) sB5[tid] = A.p[OFF_B5 + tid];
     }
-    if (tid < NOUT) sB5[tid] = p[OFF_B5 + tid];
     if (warp == 0) tc::tmem_alloc(tslot, TC_TMEM_COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
 
-    // K-chunk c (k = 64 c .. 64 c + 63, all 256 n) of layer l's packed weights into sB: the
-    // B operand's K-major layout keeps each chunk's core matrices at a fixed column range of
-    // every row group, so a chunk is 32 row groups x 8 core matrices; the packed image stores
-    // the chunks one after the other (pack_hidden_weights), one bulk copy each.
-    // weights of layer l into sB (thread 0): one 128 KB image, four bulk copies
-    auto load_weights = [&](int l) {
+    // packed operand i (0..2) into sB (thread 0): one 128 KB image, four bulk copies
+    auto load_weights = [&](int i) {
         tc::mbar_expect_tx(wbar, TC_B_BYTES);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             tc::bulk_g2s(b_base + c * (TC_B_BYTES / 4),
-                         wpack + (size_t)(l - 2) * HID * HID + c * (HID * HID / 4),
-                         TC_B_BYTES / 4, wbar);
+                         A.wpack + (size_t)i * HID * HID + c * (HID * HID / 4), TC_B_BYTES / 4,
+                         wbar);
     };
     uint32_t wphase = 0, mphase = 0;
     bool w_pending = false, m_pending = false, failed = false;
     if (tid == 0 && blockIdx.x < n_tiles) {
-        load_weights(2);
+        load_weights(0);
         w_pending = true;
     }
     const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, HID);
-    const int row = tid & (TC_ROWS - 1), cg1 = tid >> 7;  // layer 1: row, column group
+    const int row = tid & (TC_ROWS - 1), cg1 = tid >> 7;  // tile input: row, column group
     const int lg = warp & 3, cg = warp >> 2;               // epilogue: TMEM lanes, column group
     const int r = 32 * lg + lane;                          // epilogue row
 
     auto load_x = [&](int64_t tile) {
         const int64_t gr = tile * TC_ROWS + row;
-        return (tile < n_tiles && gr < n_rows) ? *reinterpret_cast<const float4 *>(x + gr * NIN)
-                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (MODE == TC_BWD) {
+            return make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            return (tile < n_tiles && gr < n_rows)
+                       ? *reinterpret_cast<const float4 *>(A.x + gr * NIN)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
     float4 x_next = load_x(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < n_tiles && !failed; tile += gridDim.x) {
-        // ---- layer 1: row `row`, columns cg1 * 64 .. +63 ------------------------------------
+        // ---- tile input: row `row`, columns cg1 * 64 .. +63 -------------------------------
         {
-            const float4 xi = x_next;
-            x_next = load_x(tile + gridDim.x);  // in flight through this tile's layers
+            const int64_t gr = tile * TC_ROWS + row;
+            const bool in = gr < n_rows;
+            if constexpr (MODE == TC_BWD) {  // dZ_4 from HBM
 #pragma unroll 2
-            for (int c = 0; c < TC_COLS / 8; ++c) {
-                const int n0 = cg1 * TC_COLS + c * 8;
-                float h[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 w = sW1[n0 + j];
-                    h[j] = silu_fast(sBias[n0 + j] + xi.x * w.x + xi.y * w.y + xi.z * w.z +
-                                     xi.w * w.w);
+                for (int c = 0; c < TC_COLS / 8; ++c) {
+                    const int n0 = cg1 * TC_COLS + c * 8;
+                    const uint4 v = in ? *reinterpret_cast<const uint4 *>(A.dZ4 + gr * HID + n0)
+                                       : make_uint4(0u, 0u, 0u, 0u);
+                    *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(row, n0, HID)) = v;
                 }
-                *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(row, n0, HID)) =
-                    make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
-                               pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+            } else {  // layer 1 (4 -> 256) on CUDA cores
+                const float4 xi = x_next;
+                x_next = load_x(tile + gridDim.x);  // in flight through this tile's layers
+#pragma unroll 2
+                for (int c = 0; c < TC_COLS / 8; ++c) {
+                    const int n0 = cg1 * TC_COLS + c * 8;
+                    float z[8], h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 w = sW1[n0 + j];
+                        z[j] = sBias[n0 + j] + xi.x * w.x + xi.y * w.y + xi.z * w.z + xi.w * w.w;
+                        h[j] = silu_fast(z[j]);
+                    }
+                    const uint4 hb = pack8(h);
+                    *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(row, n0, HID)) = hb;
+                    if constexpr (MODE == TC_TRAIN) {
+                        if (in) {
+                            *reinterpret_cast<uint4 *>(A.Z[1] + gr * HID + n0) = pack8(z);
+                            *reinterpret_cast<uint4 *>(A.H[1] + gr * HID + n0) = hb;
+                        }
+                    }
+                }
             }
         }
         tc::fence_proxy_async();
         float acc5[NOUT] = {0.f, 0.f, 0.f, 0.f};
-        for (int l = 2; l <= 4; ++l) {
+        for (int i = 0; i < 3; ++i) {
             // A tile written and previous accumulator reads done; weights present
             bool to = false;
             if (tid == 0 && w_pending) {
@@ -607,17 +662,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             tc::fence_after_sync();
-            if (tid == 0) {  // next weights while the epilogue runs
-                if (l < 4) {
-                    load_weights(l + 1);
+            if (tid == 0) {  // next operand while the epilogue runs
+                if (i < 2) {
+                    load_weights(i + 1);
                     w_pending = true;
                 } else if (tile + gridDim.x < n_tiles) {
-                    load_weights(2);
+                    load_weights(0);
                     w_pending = true;
                 }
             }
             // ---- epilogue: row r (TMEM lane), columns cg * 64 .. +63 ----------------------
-            const float *bias = sBias + (l - 1) * HID;
+            const int64_t gr = tile * TC_ROWS + r;
+            const bool in = gr < n_rows;
+            const int l_out = MODE == TC_BWD ? 3 - i : 2 + i;  // layer whose Z/H/dZ this writes
+            const float *bias = sBias + (l_out - 1) * HID;
             const uint32_t trow = tmem + ((uint32_t)(32 * lg) << 16);
 #pragma unroll 1
             for (int c = 0; c < TC_COLS / 16; c += 2) {
@@ -630,31 +688,67 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int u = 0; u < 2; ++u) {
                     const int nb = n0 + 16 * u;
                     float h[16];
+                    if constexpr (MODE == TC_BWD) {
+                        // dZ_{l-1} = (dZ_l W_l^T) * SiLU'(Z_{l-1})
+                        float zf[16];
 #pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4) {
-                        const float4 b4 = *reinterpret_cast<const float4 *>(bias + nb + 4 * j4);
-                        h[4 * j4 + 0] = silu_fast(__uint_as_float(v[u][4 * j4 + 0]) + b4.x);
-                        h[4 * j4 + 1] = silu_fast(__uint_as_float(v[u][4 * j4 + 1]) + b4.y);
-                        h[4 * j4 + 2] = silu_fast(__uint_as_float(v[u][4 * j4 + 2]) + b4.z);
-                        h[4 * j4 + 3] = silu_fast(__uint_as_float(v[u][4 * j4 + 3]) + b4.w);
+                        for (int q = 0; q < 2; ++q) {
+                            const uint4 zz = in ? *reinterpret_cast<const uint4 *>(
+                                                      A.Z[l_out] + gr * HID + nb + 8 * q)
+                                                : make_uint4(0u, 0u, 0u, 0u);
+                            unpack8(zz, zf + 8 * q);
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) h[j] = __uint_as_float(v[u][j]) * dsilu_fast(zf[j]);
+                    } else {
+                        float z[16];
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            const float4 b4 = *reinterpret_cast<const float4 *>(bias + nb + 4 * j4);
+                            z[4 * j4 + 0] = __uint_as_float(v[u][4 * j4 + 0]) + b4.x;
+                            z[4 * j4 + 1] = __uint_as_float(v[u][4 * j4 + 1]) + b4.y;
+                            z[4 * j4 + 2] = __uint_as_float(v[u][4 * j4 + 2]) + b4.z;
+                            z[4 * j4 + 3] = __uint_as_float(v[u][4 * j4 + 3]) + b4.w;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) h[j] = silu_fast(z[j]);
+                        if constexpr (MODE == TC_TRAIN) {
+                            if (in) {
+#pragma unroll
+                                for (int q = 0; q < 2; ++q) {
+                                    *reinterpret_cast<uint4 *>(A.Z[l_out] + gr * HID + nb + 8 * q) =
+                                        pack8(z + 8 * q);
+                                    *reinterpret_cast<uint4 *>(A.H[l_out] + gr * HID + nb + 8 * q) =
+                                        pack8(h + 8 * q);
+                                }
+                            }
+                        }
                     }
-                    if (l < 4) {
+                    if (i < 2) {  // next layer's operand
 #pragma unroll
                         for (int q = 0; q < 2; ++q)
                             *reinterpret_cast<uint4 *>(sA + tc::kmajor_offset(r, nb + 8 * q, HID)) =
-                                make_uint4(pack_bf16x2(h[8 * q + 0], h[8 * q + 1]),
-                                           pack_bf16x2(h[8 * q + 2], h[8 * q + 3]),
-                                           pack_bf16x2(h[8 * q + 4], h[8 * q + 5]),
-                                           pack_bf16x2(h[8 * q + 6], h[8 * q + 7]));
-                    } else {  // layer 5 (256 -> 4) on the BF16-rounded activations
+                                pack8(h + 8 * q);
+                    }
+                    if constexpr (MODE == TC_BWD) {
+                        if (in) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float hb = __bfloat162float(__float2bfloat16_rn(h[j]));
-                            const float4 w = sW5[nb + j];
-                            acc5[0] += hb * w.x;
-                            acc5[1] += hb * w.y;
-                            acc5[2] += hb * w.z;
-                            acc5[3] += hb * w.w;
+                            for (int q = 0; q < 2; ++q)
+                                *reinterpret_cast<uint4 *>(A.dZ[l_out] + gr * HID + nb + 8 * q) =
+                                    pack8(h + 8 * q);
+                        }
+                    }
+                    if constexpr (MODE == TC_INFER) {
+                        if (i == 2) {  // layer 5 (256 -> 4) on the BF16-rounded activations
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float hb = __bfloat162float(__float2bfloat16_rn(h[j]));
+                                const float4 w = sW5[nb + j];
+                                acc5[0] += hb * w.x;
+                                acc5[1] += hb * w.y;
+                                acc5[2] += hb * w.z;
+                                acc5[3] += hb * w.w;
+                            }
                         }
                     }
                 }
@@ -663,29 +757,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc::fence_before_sync();
         }
         if (failed) break;
-        // ---- layer 5: combine the column groups of each row ---------------------------------
-        if (cg > 0) {
+        if constexpr (MODE == TC_INFER) {
+            // ---- layer 5: combine the column groups of each row -----------------------------
+            if (cg > 0) {
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o) red[((cg - 1) * TC_ROWS + r) * NOUT + o] = acc5[o];
-        }
-        __syncthreads();
-        if (cg == 0) {
-            const int64_t gr = tile * TC_ROWS + r;
-            if (gr < n_rows) {
-                float out[NOUT];
+                for (int o = 0; o < NOUT; ++o) red[((cg - 1) * TC_ROWS + r) * NOUT + o] = acc5[o];
+            }
+            __syncthreads();
+            if (cg == 0) {
+                const int64_t gr = tile * TC_ROWS + r;
+                if (gr < n_rows) {
+                    float out[NOUT];
 #pragma unroll
-                for (int o = 0; o < NOUT; ++o) {
-                    out[o] = acc5[o] + sB5[o];
+                    for (int o = 0; o < NOUT; ++o) {
+                        out[o] = acc5[o] + sB5[o];
 #pragma unroll
-                    for (int g = 0; g < TC_CG - 1; ++g) out[o] += red[(g * TC_ROWS + r) * NOUT + o];
+                        for (int g = 0; g < TC_CG - 1; ++g) out[o] += red[(g * TC_ROWS + r) * NOUT + o];
+                    }
+                    *reinterpret_cast<float4 *>(A.y + gr * NOUT) =
+                        make_float4(out[0], out[1], out[2], out[3]);
                 }
-                *reinterpret_cast<float4 *>(y + gr * NOUT) = make_float4(out[0], out[1], out[2], out[3]);
             }
         }
     }
     // ---- teardown: nothing of ours in flight, then free the tensor memory -------------------
     if (tid == 0) {
-        if (failed) atomicExch(err, 1);
+        if (failed) atomicExch(A.err, 1);
         // bounded waits for our own MMAs and copies still in flight
         if (m_pending) tc::mbar_wait(mbar, mphase, TC_WAIT);
         if (w_pending) tc::mbar_wait(wbar, wphase, TC_WAIT);
@@ -705,58 +802,76 @@ void gemm(const bf16 *A, const bf16 *B, int M, int N, int K, int lda, int ldb, i
     gemm_bf16_kernel<A_T, B_T, EPI><<<grid, GEMM_THREADS, 0, st>>>(A, B, M, N, K, lda, ldb, kps, ep);
 }
 
-// Forward pass over B rows (B multiple of 128).  With t: loss and dL/dy as well.
-void forward(odx_mlp *m, const float *x, int64_t B, int64_t B_true, float *Y, const float *t,
-             bool keep_z, cudaStream_t st)
+template <int MODE>
+void launch_chain(odx_mlp *m, const TcArgs &a, int64_t n, cudaStream_t st)
 {
-    layer1_fwd<<<blocks_for(B * HID, 256), 256, 0, st>>>(x, m->pb, m->p, B,
-                                                       keep_z ? m->Z[1] : nullptr, m->H[1]);
-    for (int l = 2; l <= 4; ++l) {
-        EpiArgs ep{};
-        ep.bias = m->p + off_b(l);
-        ep.Z = keep_z ? m->Z[l] : nullptr;
-        ep.H = m->H[l];
-        ep.ldc = HID;
-        gemm<false, false, EPI_BIAS_SILU>(m->H[l - 1], m->pb + off_w(l), (int)B, HID, HID, HID,
-                                          HID, 1, ep, st);
+    if (n <= 0) return;
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, std::max(1, m->num_sms));
+    mlp_chain_tc<MODE><<<grid, TC_THREADS, TC_SMEM, st>>>(a);
+}
+
+TcArgs chain_args(odx_mlp *m, const bf16 *wpack, int64_t n)
+{
+    TcArgs a{};
+    a.pb = m->pb;
+    a.p = m->p;
+    a.wpack = wpack;
+    a.n_rows = n;
+    a.err = m->tc_err;
+    for (int l = 1; l <= 4; ++l) {
+        a.Z[l] = m->Z[l];
+        a.H[l] = m->H[l];
+        a.dZ[l] = m->dZ[l];
     }
+    return a;
+}
+
+// Training forward over B rows (B multiple of 128) on the tensor cores, Z_l and H_l kept;
+// then layer 5 with the loss and dL/dy (targets t).
+void forward(odx_mlp *m, const float *x, int64_t B, int64_t B_true, float *Y, const float *t,
+             cudaStream_t st)
+{
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0);
+    TcArgs a = chain_args(m, m->wpack, B);
+    a.x = x;
+    launch_chain<TC_TRAIN>(m, a, B, st);
     layer5_fwd_loss<<<blocks_for(B * 32, 256), 256, 0, st>>>(m->H[4], m->pb, m->p, B, B_true, Y,
                                                              t, m->dY, m->loss);
 }
 
-// Backward pass after forward(..., keep_z = true, t): gradients into m->grad (zeroed here).
+// Backward pass after forward(): gradients into m->grad (zeroed here).  dL/dZ through the
+// three 256 x 256 layers on the tensor cores (one chain per row tile); the weight gradients
+// dW_l = H_{l-1}^T dZ_l reduce over the batch on the mma.sync GEMM (split-K).
 void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
 {
     cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float), st);
     const unsigned rblocks = blocks_for(B, 256);
     layer5_bwd_w<<<rblocks, 256, 0, st>>>(m->H[4], m->dY, B, m->grad + OFF_W5, m->grad + OFF_B5);
-    layer5_bwd_dz<<<blocks_for(B * HID, 256), 256, 0, st>>>(m->dY, m->pb, m->Z[4], B, m->dZ);
-    bf16 *dz = m->dZ, *dz_prev = m->dZ2;
+    layer5_bwd_dz<<<blocks_for(B * HID, 256), 256, 0, st>>>(m->dY, m->pb, m->Z[4], B, m->dZ[4]);
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpackB, 1);
+    TcArgs a = chain_args(m, m->wpackB, B);
+    a.dZ4 = m->dZ[4];
+    launch_chain<TC_BWD>(m, a, B, st);
     const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
     for (int l = 4; l >= 2; --l) {
         // dW_l += H_{l-1}^T dZ_l (split-K over the batch), db_l += sum dZ_l
         EpiArgs ew{};
         ew.C32 = m->grad + off_w(l);
         ew.ldc = HID;
-        gemm<true, false, EPI_ATOMIC_F32>(m->H[l - 1], dz, HID, HID, (int)B, HID, HID, splits, ew, st);
-        bias_grad<<<rblocks, 256, 0, st>>>(dz, B, m->grad + off_b(l));
-        // dZ_{l-1} = (dZ_l W_l^T) * silu'(Z_{l-1})
-        EpiArgs ed{};
-        ed.Z = m->Z[l - 1];
-        ed.H = dz_prev;
-        ed.ldc = HID;
-        gemm<false, true, EPI_DSILU>(dz, m->pb + off_w(l), (int)B, HID, HID, HID, HID, 1, ed, st);
-        std::swap(dz, dz_prev);
+        gemm<true, false, EPI_ATOMIC_F32>(m->H[l - 1], m->dZ[l], HID, HID, (int)B, HID, HID,
+                                          splits, ew, st);
+        bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[l], B, m->grad + off_b(l));
     }
-    layer1_bwd_w<<<rblocks, 256, 0, st>>>(x, dz, B, m->grad + OFF_W1);
-    bias_grad<<<rblocks, 256, 0, st>>>(dz, B, m->grad + OFF_B1);
+    layer1_bwd_w<<<rblocks, 256, 0, st>>>(x, m->dZ[1], B, m->grad + OFF_W1);
+    bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[1], B, m->grad + OFF_B1);
 }
 
 void free_mlp(odx_mlp *m)
 {
     cudaSetDevice(m->device);
     for (void *q : {(void *)m->p, (void *)m->pb, (void *)m->grad, (void *)m->m1, (void *)m->m2,
-                    (void *)m->dZ, (void *)m->dZ2, (void *)m->Y, (void *)m->dY, (void *)m->loss,
+                    (void *)m->Y, (void *)m->dY, (void *)m->loss, (void *)m->wpackB,
                     (void *)m->xin, (void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays,
                     (void *)m->fb_pix, (void *)m->fb_count, (void *)m->bcrit,
                     (void *)m->scene_tab, (void *)m->wpack, (void *)m->tc_err})
@@ -764,6 +879,7 @@ void free_mlp(odx_mlp *m)
     for (int l = 1; l <= 4; ++l) {
         if (m->Z[l]) cudaFree(m->Z[l]);
         if (m->H[l]) cudaFree(m->H[l]);
+        if (m->dZ[l]) cudaFree(m->dZ[l]);
     }
     delete m;
 }
@@ -785,10 +901,11 @@ int32_t take_tc_flag(odx_mlp *m)
 void infer_tc(odx_mlp *m, const float *x, int64_t n, float *y, cudaStream_t st)
 {
     if (n <= 0) return;
-    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack);
-    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, std::max(1, m->num_sms));
-    mlp_forward_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(x, m->pb, m->p, m->wpack, n, y, m->tc_err);
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0);
+    TcArgs a = chain_args(m, m->wpack, n);
+    a.x = x;
+    a.y = y;
+    launch_chain<TC_INFER>(m, a, n, st);
 }
 
 }  // namespace
@@ -812,7 +929,7 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
               cudaMalloc(&m->grad, NPARAM * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->m1, NPARAM * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->m2, NPARAM * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&m->dZ, act) == cudaSuccess && cudaMalloc(&m->dZ2, act) == cudaSuccess &&
+              cudaMalloc(&m->wpackB, (size_t)3 * HID * HID * sizeof(bf16)) == cudaSuccess &&
               cudaMalloc(&m->Y, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->dY, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
@@ -823,14 +940,19 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
               cudaMalloc(&m->wpack, (size_t)3 * HID * HID * sizeof(bf16)) == cudaSuccess &&
               cudaMalloc(&m->tc_err, sizeof(int)) == cudaSuccess;
     for (int l = 1; l <= 4 && ok; ++l)
-        ok = cudaMalloc(&m->Z[l], act) == cudaSuccess && cudaMalloc(&m->H[l], act) == cudaSuccess;
+        ok = cudaMalloc(&m->Z[l], act) == cudaSuccess && cudaMalloc(&m->H[l], act) == cudaSuccess &&
+             cudaMalloc(&m->dZ[l], act) == cudaSuccess;
     if (!ok) {
         free_mlp(m);
         return ODX_ERR_CUDA;
     }
     cudaMemset(m->m1, 0, NPARAM * sizeof(float));
     cudaMemset(m->m2, 0, NPARAM * sizeof(float));
-    if (cudaFuncSetAttribute(mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(mlp_chain_tc<TC_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_chain_tc<TC_TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_chain_tc<TC_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TC_SMEM) != cudaSuccess ||
         cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) !=
             cudaSuccess ||
@@ -888,10 +1010,11 @@ int32_t odx_mlp_forward(odx_mlp *m, const float *x, int64_t n, float *y, void *s
 int32_t odx_mlp_gradients(odx_mlp *m, const float *x, const float *t, int64_t n, float *grad_host,
                           float *loss_host)
 {
-    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0) return ODX_ERR_INVALID_ARG;
+    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || ((uintptr_t)x & 15u))
+        return ODX_ERR_INVALID_ARG;
     MLP_CUDA(cudaSetDevice(m->device));
     MLP_CUDA(cudaMemset(m->loss, 0, sizeof(float)));
-    forward(m, x, n, n, m->Y, t, true, nullptr);
+    forward(m, x, n, n, m->Y, t, nullptr);
     backward(m, x, n, nullptr);
     MLP_CUDA(cudaDeviceSynchronize());
     if (grad_host)
@@ -903,12 +1026,13 @@ int32_t odx_mlp_gradients(odx_mlp *m, const float *x, const float *t, int64_t n,
 int32_t odx_mlp_train_step(odx_mlp *m, const float *x, const float *t, int64_t n, float lr,
                            float *loss_dev, void *stream)
 {
-    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || !(lr > 0.f))
+    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || !(lr > 0.f) ||
+        ((uintptr_t)x & 15u))
         return ODX_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CUDA(cudaSetDevice(m->device));
     MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
-    forward(m, x, n, n, m->Y, t, true, st);
+    forward(m, x, n, n, m->Y, t, st);
     backward(m, x, n, st);
     m->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;
