@@ -296,13 +296,19 @@ int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Ad
  * FP32 accumulator in tensor memory); x_dev and y_dev 16-byte aligned (else INVALID_ARG).
  * Asynchronous on `stream`.  A tensor-core wait that times out leaves its tile's outputs
  * unwritten and raises a device flag, reported (and cleared) as ODX_ERR_DEVICE_FLAG by the
- * next odx_mlp_get_params or odx_surrogate_render call. */
+ * next odx_mlp_get_params, odx_mlp_gradients or odx_surrogate_render call. */
 int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
-/* Loss and gradients (dL/dparams, layout as the parameters) of one batch, n a multiple of
- * 128 and <= max_batch; synchronous, results copied to host (either may be NULL). */
+/* Training rows: x_dev[n][4] = (alpha / 20, beta / 20, a, cos i), 16-byte aligned;
+ * t_dev[n][8] as written by odx_mlp_targets (captured flag, log r_cross, phi_cross / pi, g,
+ * crossing mask, g mask, 0, 0).  Both device pointers, caller-owned.
+ * Loss and gradients (dL/dparams, layout as the parameters) of one batch, n a multiple of
+ * 128 and <= max_batch; synchronous, results copied to host (either may be NULL); returns
+ * ODX_ERR_DEVICE_FLAG if a tensor-core wait timed out in this or an earlier call. */
 int32_t odx_mlp_gradients(odx_mlp *mlp, const float *x_dev, const float *t_dev, int64_t n,
                           float *grad_host, float *loss_host);
-/* One Adam step on a batch (n a multiple of 128, <= max_batch); loss_dev: 1 float or NULL. */
+/* One Adam step on a batch (n a multiple of 128, <= max_batch; x_dev, t_dev as above);
+ * loss_dev: 1 float or NULL.  Asynchronous on `stream`; a tensor-core time-out is reported
+ * by the next odx_mlp_get_params or odx_mlp_gradients call. */
 int32_t odx_mlp_train_step(odx_mlp *mlp, const float *x_dev, const float *t_dev, int64_t n,
                            float lr, float *loss_dev, void *stream);
 /* Inputs and targets from traced rays (odx_trace_rays with a thin-disk prototype):

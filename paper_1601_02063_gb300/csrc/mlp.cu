@@ -1,9 +1,10 @@
 // Learned thin-disk transfer function (alpha, beta, a, cos i) -> (capture logit, log r_cross,
 // phi_cross / pi, g): 4 -> 256 -> 256 -> 256 -> 256 -> 4 with SiLU, BF16 weights and
-// activations, FP32 accumulation.  Training (forward, backward, Adam) runs in the kernels
-// below, the 256 x 256 layers on the BF16 mma.sync GEMM of mlp_gemm.cuh and the 4-wide input
-// and output layers on CUDA cores; inference is one fused kernel per 128-row tile on the
-// tcgen05 tensor cores (mlp_chain_tc, accumulator in tensor memory).  The surrogate render
+// activations, FP32 accumulation.  The 256 x 256 layers run on the tcgen05 tensor cores
+// (accumulators in tensor memory): inference and the training forward pass as one fused
+// chain per 128-row tile (mlp_chain_tc), the backward dL/dZ chain the same way, and the
+// weight gradients as batch-reduction MMAs (mlp_dw_tc); the 4-wide input and output layers
+// and Adam run on CUDA cores.  The surrogate render
 // classifies each pixel and hands the uncertain ones (near the Bardeen critical curve or
 // with an unsure capture probability) back to the ray tracer.
 #include <cuda_bf16.h>
@@ -16,7 +17,6 @@
 #include <vector>
 
 #include "kerr_device.cuh"
-#include "mlp_gemm.cuh"
 #include "odx_internal.h"
 #include "tcgen05.cuh"
 
@@ -34,7 +34,6 @@ int32_t ctx_view(odx_ctx *ctx, CtxView *v);
 }  // namespace odx
 
 using namespace odx;
-using namespace odx::mlp;
 using bf16 = __nv_bfloat16;
 
 namespace {
@@ -52,6 +51,24 @@ static_assert(NPARAM == ODX_MLP_PARAMS, "parameter count");
 __host__ __device__ constexpr int off_w(int l) { return OFF_W2 + (l - 2) * LAYER_SZ; }  // l = 2..4
 __host__ __device__ constexpr int off_b(int l) { return off_w(l) + HID * HID; }
 
+// 16-byte global -> shared copies (cp.async groups), used to stage the weight-gradient operands
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+                 "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// d silu(z) / dz = s (1 + z (1 - s)), s = 1 / (1 + e^-z)
+__device__ __forceinline__ float dsilu(float z)
+{
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
 }  // namespace
 
 struct odx_mlp {
@@ -68,7 +85,8 @@ struct odx_mlp {
     float *xin = nullptr;   // padded input rows for inference
     bf16 *wpack = nullptr;   // hidden-layer weights as forward tensor-core operands (W^T)
     bf16 *wpackB = nullptr;  // ... and as backward operands (W)
-    int *tc_err = nullptr;  // set by the inference kernel if a wait timed out
+    float *dw_part = nullptr;  // per-split weight-gradient partial sums
+    int *tc_err = nullptr;  // set by a tensor-core kernel whose wait timed out
     int num_sms = 0;
     // surrogate render workspace
     int64_t surr_cap = 0;
@@ -793,13 +811,155 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
     if (warp == 0) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
-template <bool A_T, bool B_T, int EPI>
-void gemm(const bf16 *A, const bf16 *B, int M, int N, int K, int lda, int ldb, int splits,
-          EpiArgs ep, cudaStream_t st)
+// ---- weight gradients on tcgen05: dW_l = H_{l-1}^T dZ_l --------------------------------------
+// The batch index is the reduction index and the row index of both operands in HBM, so both
+// are MN-major for the tensor core: a 16-byte piece of one row (8 consecutive features) is one
+// core-matrix row.  Grid (splits, 3 layers); each CTA reduces a contiguous run of 64-row
+// chunks through a three-stage cp.async ring into two 128 x 256 FP32 accumulators (all 512
+// tensor-memory columns: features 0-127 and 128-255 of H), then writes its partial sum; a
+// second kernel adds the partials in split order (deterministic).
+constexpr int DW_THREADS = 256, DW_KC = 64, DW_STAGES = 3, DW_MAX_SPLITS = 48;
+constexpr uint32_t DW_OP_BYTES = HID * DW_KC * 2;                 // one operand chunk, 32 KB
+constexpr uint32_t DW_LBO = (HID / 8) * 128;                      // K (batch) core stride
+constexpr size_t DW_SMEM = 1024 + (size_t)DW_STAGES * 2 * DW_OP_BYTES + 64;
+static_assert(DW_SMEM <= 232448, "shared memory of one CTA");
+
+struct DwArgs {
+    const bf16 *H[3], *dZ[3];  // per layer slot: H_{l-1}, dZ_l (row-major [B][256]) for l = 4, 3, 2
+    int64_t n_chunks;          // B / 64
+    float *part;               // [3][splits][256][256]
+    int *err;
+};
+
+__global__ void __launch_bounds__(DW_THREADS, 1) mlp_dw_tc(const __grid_constant__ DwArgs A)
 {
-    const int kps = ((K / splits + BK - 1) / BK) * BK;
-    dim3 grid(N / BN, M / BM, (K + kps - 1) / kps);
-    gemm_bf16_kernel<A_T, B_T, EPI><<<grid, GEMM_THREADS, 0, st>>>(A, B, M, N, K, lda, ldb, kps, ep);
+    extern __shared__ __align__(16) unsigned char dw_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(((uintptr_t)dw_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + (size_t)DW_STAGES * 2 * DW_OP_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + DW_STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int layer = blockIdx.y, splits = gridDim.x, s = blockIdx.x;
+    const bf16 *Hg = A.H[layer], *Zg = A.dZ[layer];
+    const int64_t c0 = A.n_chunks * s / splits, c1 = A.n_chunks * (s + 1) / splits;
+    const int nc = (int)(c1 - c0);
+    uint32_t mbar[DW_STAGES];
+#pragma unroll
+    for (int i = 0; i < DW_STAGES; ++i) mbar[i] = tc::smem_u32(&bars[i]);
+    if (tid == 0) {
+        for (int i = 0; i < DW_STAGES; ++i) tc::mbar_init(mbar[i], 1);
+        tc::mbar_fence_init();
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // chunk c of this CTA into stage st: rows 64 c .. +63 of H and dZ, 2 x 2048 pieces of 16 B
+    auto load_chunk = [&](int c, int st) {
+        unsigned char *a = sm + (size_t)st * 2 * DW_OP_BYTES, *b = a + DW_OP_BYTES;
+        const int64_t row0 = (c0 + c) * DW_KC;
+#pragma unroll
+        for (int q = 0; q < 2048 / DW_THREADS; ++q) {
+            const int piece = tid + q * DW_THREADS;
+            const int r = piece >> 5, g = piece & 31;  // row in chunk, feature group
+            const uint32_t off = g * 128 + (r >> 3) * DW_LBO + (r & 7) * 16;
+            cp_async16(a + off, Hg + (row0 + r) * HID + g * 8);
+            cp_async16(b + off, Zg + (row0 + r) * HID + g * 8);
+        }
+    };
+    uint32_t mph = 0;  // parity bits of the stage barriers (bit i: next completion of stage i)
+    bool failed = false, pending = false;
+    int last_st = 0;   // stage barrier of the most recent commit
+#pragma unroll
+    for (int i = 0; i < DW_STAGES - 1; ++i) {
+        if (i < nc) load_chunk(i, i);
+        cp_async_commit();
+    }
+    const uint32_t idesc = tc::idesc_bf16_f32(128, HID, true, true);
+    for (int c = 0; c < nc; ++c) {
+        const int st = c % DW_STAGES;
+        cp_async_wait<DW_STAGES - 2>();  // chunk c landed (this thread's pieces)
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t a = tc::smem_u32(sm + (size_t)st * 2 * DW_OP_BYTES), b = a + DW_OP_BYTES;
+#pragma unroll
+            for (int j = 0; j < DW_KC / 16; ++j)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    tc::mma_bf16(tmem + h * 256,
+                                 tc::smem_desc(a + h * 16 * 128 + 2 * j * DW_LBO, DW_LBO, 128),
+                                 tc::smem_desc(b + 2 * j * DW_LBO, DW_LBO, 128), idesc,
+                                 (c > 0 || j > 0) ? 1u : 0u);
+            tc::mma_commit(mbar[st]);
+            pending = true;
+            last_st = st;
+        }
+        // refill the stage chunk c - 1 used, once its MMAs are done
+        const int cn = c + DW_STAGES - 1, sn = cn % DW_STAGES;
+        bool to = false;
+        if (tid == 0 && c >= 1 && cn < nc) {
+            to = !tc::mbar_wait(mbar[sn], (mph >> sn) & 1u, TC_WAIT);
+            if (!to) mph ^= 1u << sn;
+        }
+        if (__syncthreads_or(to)) {
+            failed = true;
+            break;
+        }
+        if (cn < nc) load_chunk(cn, sn);
+        cp_async_commit();
+    }
+    cp_async_wait<0>();  // none of our copies outstanding
+    // all MMAs complete: the last commit covers the earlier ones (earlier phases of its
+    // barrier were waited for by the refills)
+    bool to = false;
+    if (tid == 0 && pending) {
+        to = !tc::mbar_wait(mbar[last_st], (mph >> last_st) & 1u, TC_WAIT);
+        pending = to;
+    }
+    if (__syncthreads_or(to) || failed) {
+        if (tid == 0) atomicExch(A.err, 1);
+        failed = true;
+    }
+    tc::fence_after_sync();
+    if (!failed) {
+        // rows k = 128 (warp / 4) + 32 (warp % 4) + lane of the partial, 256 columns
+        const int h = warp >> 2, k = 128 * h + 32 * (warp & 3) + lane;
+        float *out = A.part + (((size_t)layer * splits + s) * HID + k) * HID;
+        const uint32_t trow = tmem + h * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
+        for (int c = 0; c < HID; c += 16) {
+            uint32_t v[16];
+            tc::tmem_ld16(trow + c, v);
+            tc::tmem_ld_wait();
+            if (nc == 0)
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<float4 *>(out + c + 4 * q) =
+                    make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// grad_W[l] = sum over splits of the partials, in split order
+__global__ void dw_reduce(const float *__restrict__ part, int splits, float *__restrict__ grad)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 3 * HID * HID) return;
+    const int slot = (int)(idx / (HID * HID)), e = (int)(idx % (HID * HID));
+    const int l = 4 - slot;
+    float sum = 0.f;
+    for (int q = 0; q < splits; ++q) sum += part[((size_t)slot * splits + q) * HID * HID + e];
+    grad[off_w(l) + e] = sum;
 }
 
 template <int MODE>
@@ -842,7 +1002,8 @@ void forward(odx_mlp *m, const float *x, int64_t B, int64_t B_true, float *Y, co
 
 // Backward pass after forward(): gradients into m->grad (zeroed here).  dL/dZ through the
 // three 256 x 256 layers on the tensor cores (one chain per row tile); the weight gradients
-// dW_l = H_{l-1}^T dZ_l reduce over the batch on the mma.sync GEMM (split-K).
+// dW_l = H_{l-1}^T dZ_l reduce over the batch on the tensor cores too (split over the batch,
+// partials added in split order).
 void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
 {
     cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float), st);
@@ -853,16 +1014,19 @@ void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
     TcArgs a = chain_args(m, m->wpackB, B);
     a.dZ4 = m->dZ[4];
     launch_chain<TC_BWD>(m, a, B, st);
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, B / 512));
-    for (int l = 4; l >= 2; --l) {
-        // dW_l += H_{l-1}^T dZ_l (split-K over the batch), db_l += sum dZ_l
-        EpiArgs ew{};
-        ew.C32 = m->grad + off_w(l);
-        ew.ldc = HID;
-        gemm<true, false, EPI_ATOMIC_F32>(m->H[l - 1], m->dZ[l], HID, HID, (int)B, HID, HID,
-                                          splits, ew, st);
-        bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[l], B, m->grad + off_b(l));
+    // dW_l = H_{l-1}^T dZ_l for l = 4, 3, 2 on the tensor cores, split over the batch
+    DwArgs dw{};
+    for (int slot = 0; slot < 3; ++slot) {
+        dw.H[slot] = m->H[3 - slot];
+        dw.dZ[slot] = m->dZ[4 - slot];
     }
+    dw.n_chunks = B / DW_KC;
+    dw.part = m->dw_part;
+    dw.err = m->tc_err;
+    const int splits = (int)std::min<int64_t>(DW_MAX_SPLITS, dw.n_chunks);
+    mlp_dw_tc<<<dim3((unsigned)splits, 3), DW_THREADS, DW_SMEM, st>>>(dw);
+    dw_reduce<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->dw_part, splits, m->grad);
+    for (int l = 4; l >= 2; --l) bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[l], B, m->grad + off_b(l));
     layer1_bwd_w<<<rblocks, 256, 0, st>>>(x, m->dZ[1], B, m->grad + OFF_W1);
     bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[1], B, m->grad + OFF_B1);
 }
@@ -872,6 +1036,7 @@ void free_mlp(odx_mlp *m)
     cudaSetDevice(m->device);
     for (void *q : {(void *)m->p, (void *)m->pb, (void *)m->grad, (void *)m->m1, (void *)m->m2,
                     (void *)m->Y, (void *)m->dY, (void *)m->loss, (void *)m->wpackB,
+                    (void *)m->dw_part,
                     (void *)m->xin, (void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays,
                     (void *)m->fb_pix, (void *)m->fb_count, (void *)m->bcrit,
                     (void *)m->scene_tab, (void *)m->wpack, (void *)m->tc_err})
@@ -886,7 +1051,7 @@ void free_mlp(odx_mlp *m)
 
 int64_t round128(int64_t n) { return (n + 127) / 128 * 128; }
 
-// Report and clear the inference kernel's time-out flag (synchronous).
+// Report and clear the tensor-core kernels' time-out flag (synchronous).
 int32_t take_tc_flag(odx_mlp *m)
 {
     int h = 0;
@@ -930,6 +1095,8 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
               cudaMalloc(&m->m1, NPARAM * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->m2, NPARAM * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->wpackB, (size_t)3 * HID * HID * sizeof(bf16)) == cudaSuccess &&
+              cudaMalloc(&m->dw_part, (size_t)3 * DW_MAX_SPLITS * HID * HID * sizeof(float)) ==
+                  cudaSuccess &&
               cudaMalloc(&m->Y, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->dY, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
@@ -954,6 +1121,8 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
                              (int)TC_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(mlp_chain_tc<TC_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TC_SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(mlp_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)DW_SMEM) != cudaSuccess ||
         cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) !=
             cudaSuccess ||
         cudaMemset(m->tc_err, 0, sizeof(int)) != cudaSuccess) {
@@ -1020,7 +1189,7 @@ int32_t odx_mlp_gradients(odx_mlp *m, const float *x, const float *t, int64_t n,
     if (grad_host)
         MLP_CUDA(cudaMemcpy(grad_host, m->grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
     if (loss_host) MLP_CUDA(cudaMemcpy(loss_host, m->loss, sizeof(float), cudaMemcpyDeviceToHost));
-    return ODX_OK;
+    return take_tc_flag(m);
 }
 
 int32_t odx_mlp_train_step(odx_mlp *m, const float *x, const float *t, int64_t n, float lr,

@@ -2,11 +2,15 @@
 // MMA with the accumulator in tensor memory, loads back to registers), mbarriers and the
 // bulk (non-tensor) asynchronous copy, as inline PTX.  Used by the MLP inference kernel.
 //
-// Operand layout used here (K-major, no swizzle): a matrix of R rows and K columns of BF16
-// is stored as 8 x 8 "core matrices" (8 rows x 16 bytes, 128 contiguous bytes); core matrix
-// (row group i, column group j) starts at i * SBO + j * LBO bytes, with LBO = 128 and
-// SBO = (K / 8) * 128, so the element (r, k) sits at byte
-//   (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// Operand layouts used here (no swizzle), both built from 8 x 8 "core matrices" of BF16
+// (128 contiguous bytes); LBO is the byte stride between core matrices along K, SBO along
+// M (or N):
+// - K-major: a core matrix is 8 rows (M or N) x 16 bytes (8 consecutive k); with LBO = 128
+//   and SBO = (K / 8) * 128 the element (r, k) sits at byte
+//   (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+// - MN-major: a core matrix is 8 rows (k) x 16 bytes (8 consecutive m or n), element (r, k)
+//   at (r / 8) * SBO + (k / 8) * LBO + (k % 8) * 16 + (r % 8) * 2 (checked on the GPU
+//   against a CPU product).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,15 +42,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B (both K-major), FP32 accumulator,
-// M x N tile.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N)
+// Instruction descriptor of kind::f16: BF16 A and B (K-major unless a_mn / b_mn), FP32
+// accumulator, M x N tile.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N, bool a_mn = false,
+                                                      bool b_mn = false)
 {
-    return (1u << 4)            // D format: F32
-           | (1u << 7)          // A format: BF16
-           | (1u << 10)         // B format: BF16
-           | ((N >> 3) << 17)   // N / 8
-           | ((M >> 4) << 24);  // M / 16
+    return (1u << 4)                  // D format: F32
+           | (1u << 7)                // A format: BF16
+           | (1u << 10)               // B format: BF16
+           | ((a_mn ? 1u : 0u) << 15) // A MN-major
+           | ((b_mn ? 1u : 0u) << 16) // B MN-major
+           | ((N >> 3) << 17)         // N / 8
+           | ((M >> 4) << 24);        // M / 16
 }
 
 // ---- tensor memory ------------------------------------------------------------------------
