@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 MAX_FREQ = 8
 
 STATUS = {"running": 0, "escaped": 1, "captured": 2, "disk_hit": 3, "maxsteps": 4, "numerr": 5}
-EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4}
+EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4, "synch": 5}
 CONVENTIONS = {"physical": 0, "literal": 1}
 
 
@@ -54,6 +54,7 @@ class Scene(C.Structure):
         ("rtol", C.c_double), ("h0", C.c_double), ("hmax_frac", C.c_double),
         ("horizon_factor", C.c_double),
         ("max_steps", C.c_int32), ("convention", C.c_int32),
+        ("n_e0", C.c_double), ("beta_B", C.c_double), ("mass", C.c_double),
     ]
 
 
@@ -94,6 +95,9 @@ def lib():
             "orc_nt_flux": (D, [D, D]),
             "orc_circ_E": (D, [D, D]),
             "orc_circ_L": (D, [D, D]),
+            "orc_bessel_k2": (D, [D]),
+            "orc_r_g": (D, [D]),
+            "orc_synch_coeffs": (None, [P(Scene), D, D, D, P(D), P(D)]),
             "orc_ck_tableau": (None, [P(D), P(D), P(D), P(D)]),
             "orc_pixel_center": (None, [P(Scene), I32, I32, P(D), P(D)]),
             "orc_observer_point": (None, [P(Scene), D, D, P(D)]),
@@ -136,6 +140,9 @@ def make_scene(d: dict) -> Scene:
         sc.freqs[i] = float(f)
     sc.max_steps = int(d["max_steps"])
     sc.convention = CONVENTIONS[d.get("convention", "physical")]
+    sc.n_e0 = float(d.get("n_e0", 0.0))
+    sc.beta_B = float(d.get("beta_B", 0.0))
+    sc.mass = float(d.get("mass", 0.0))
     cn = d.get("C_norm")
     if cn is None:
         cn = torus_norm(d["a"], d.get("nu_norm", 1.0), d["ne_index"], d["T0"], d["T_index"],
@@ -205,7 +212,7 @@ def geodesic_rhs(a: float, L: float, y) -> np.ndarray:
 
 def trace_path(scene: dict, alpha: float, beta: float, max_pts: int = 200000):
     sc = make_scene(scene)
-    n_comp = 6 + (2 * sc.n_freq if sc.emitter in (2, 3) else 0)
+    n_comp = 6 + (2 * sc.n_freq if sc.emitter in (2, 3, 5) else 0)
     s = np.zeros(max_pts)
     y = np.zeros((max_pts, n_comp))
     npts = C.c_int32()
@@ -233,6 +240,25 @@ def isco(a: float) -> float:
 def nt_flux(a: float, r: float) -> float:
     """8 pi F(r) / 3 of the Novikov-Thorne disk (Page-Thorne integral by quadrature)."""
     return lib().orc_nt_flux(float(a), float(r))
+
+
+def bessel_k2(x: float) -> float:
+    """K_2(x) by quadrature of its integral definition."""
+    return lib().orc_bessel_k2(float(x))
+
+
+def r_g(mass: float) -> float:
+    """G M / c^2 in cm for a mass in solar masses."""
+    return lib().orc_r_g(float(mass))
+
+
+def synch_coeffs(scene: dict, r: float, cost: float, nu0: float) -> tuple[float, float]:
+    """(j_nu, alpha_nu) of the synchrotron shell in the fluid frame, CGS."""
+    sc = make_scene(scene)
+    j, al = C.c_double(), C.c_double()
+    lib().orc_synch_coeffs(C.byref(sc), float(r), float(cost), float(nu0), C.byref(j),
+                           C.byref(al))
+    return j.value, al.value
 
 
 def circ_E(a: float, r: float) -> float:

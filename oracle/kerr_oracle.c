@@ -25,6 +25,7 @@
 #define N_GEO 6
 #define N_MAX (N_GEO + 2 * ORC_MAX_FREQ)
 #define SIN_FLOOR 1e-8 /* Section 2.1: sin(theta) is set to 1e-8 when it falls below 1e-8 */
+#define M_PI_ORC 3.14159265358979323846
 
 /* ------------------------------------------------------------------ */
 /* Closed forms of the Kerr geometry                                  */
@@ -289,6 +290,120 @@ double orc_nt_flux(double a, double r)
     return (double)(2.0L * f / (3.0L * r)); /* 8 pi F / 3 with F = f / (4 pi r) */
 }
 
+/* ------------------------------------------------------------------ */
+/* Thermal synchrotron shell (Section 4.5), CGS units                  */
+/* ------------------------------------------------------------------ */
+#define CGS_C 2.99792458e10        /* speed of light, cm s^-1 (exact)          */
+#define CGS_E 4.803204712570263e-10 /* elementary charge, esu                   */
+#define CGS_ME 9.1093837015e-28     /* electron mass, g                         */
+#define CGS_MP 1.67262192369e-24    /* proton mass, g                           */
+#define CGS_H 6.62607015e-27        /* Planck constant, erg s (exact)           */
+#define CGS_GMSUN 1.3271244e26      /* G M_sun, cm^3 s^-2 (IAU nominal)          */
+
+static long double k2_integrand(long double x, long double t)
+{ /* exp(-x (cosh t - 1)) cosh 2t: the integrand of K_2 without its factor exp(-x) */
+    return expl(-x * (coshl(t) - 1.0L)) * coshl(2.0L * t);
+}
+
+/* Nodes and weights of the 16-point Gauss-Legendre rule on [-1, 1]: the roots of P_16 by
+ * Newton's method from the usual cosine guesses, w = 2 / ((1 - x^2) P_16'(x)^2). */
+static void gauss_legendre16(long double x[16], long double w[16])
+{
+    const int n = 16;
+    for (int i = 0; i < n / 2; ++i) {
+        long double z = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+        long double dp = 1.0L;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1.0L, p1 = z; /* P_0, P_1 -> P_n by the three-term recurrence */
+            for (int k = 2; k <= n; ++k) {
+                long double p2 = ((2.0L * k - 1.0L) * z * p1 - (k - 1.0L) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0L);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (fabsl(dz) < 1e-19L) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0L / ((1.0L - z * z) * dp * dp);
+    }
+}
+
+/* Modified Bessel function of the second kind of order 2, from its integral representation
+ * K_n(x) = int_0^inf exp(-x cosh t) cosh(n t) dt (x > 0): 16-point Gauss-Legendre on eight
+ * equal panels of [0, t_max], t_max where the integrand has fallen below e^-45 of its value
+ * at 0 (relative error ~1e-15 against a library K_2 for 1e-3 <= x <= 100). */
+double orc_bessel_k2(double x)
+{
+    if (!(x > 0.0)) return NAN;
+    long double xl = x, hi = 1.0L;
+    while (xl * (coshl(hi) - 1.0L) - 2.0L * hi < 45.0L) hi += 0.25L;
+    long double gx[16], gw[16];
+    gauss_legendre16(gx, gw);
+    long double integral = 0.0L, width = hi / 8.0L;
+    for (int p = 0; p < 8; ++p) {
+        long double mid = (p + 0.5L) * width;
+        for (int i = 0; i < 16; ++i)
+            integral += 0.5L * width * gw[i] * k2_integrand(xl, mid + 0.5L * width * gx[i]);
+    }
+    return (double)(expl(-xl) * integral);
+}
+
+/* Gravitational radius G M / c^2 in cm for a mass in solar masses. */
+double orc_r_g(double mass) { return CGS_GMSUN * mass / (CGS_C * CGS_C); }
+
+/* Section 4.5: thermal synchrotron emissivity of a relativistic Maxwellian (the angle-
+ * averaged fit of Mahadevan et al. 1996 that the paper prints),
+ *   j_nu = nu 4 pi n e^2 / (sqrt(3) c K_2(1/Theta_e)) M(x_M),  x_M = nu / nu_c,
+ *   M(x) = 4.0505 x^-1/6 (1 + 0.40 x^-1/4 + 0.5316 x^-1/2) exp(-1.8899 x^1/3),
+ *   nu_c = 3 e B / (4 pi m_e c) Theta_e^2,
+ * and the absorption coefficient from Kirchhoff's law, alpha_nu = j_nu / B_nu(T_e).
+ * reading: the printed j_nu is the emissivity integrated over all directions (its integral
+ * over nu is the synchrotron power of a Maxwell-Juttner electron, (4/3) sigma_T c U_B
+ * <gamma^2 beta^2>); the transfer equation and Kirchhoff's law take the emissivity per
+ * steradian, j_nu / 4 pi, which is what this function returns.
+ * reading: the density and temperature follow power laws in r with the torus's polar
+ * profile, and B from equipartition with a fraction of the ions' virial energy,
+ * B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r) (the profiles of the cited shell model are not
+ * printed); no emission beyond r_out. */
+typedef struct {
+    double n, Theta, nu_c, K2; /* n_e [cm^-3], Theta_e, nu_c [Hz], K_2(1 / Theta_e) */
+} synch_local;
+
+static synch_local synch_at(const orc_scene *sc, double r, double cost)
+{
+    synch_local q;
+    double w = sc->theta_width;
+    q.n = sc->n_e0 * pow(r, -sc->ne_index) * exp(-cost * cost / (2.0 * w * w));
+    q.Theta = sc->T0 * pow(r, -sc->T_index);
+    double B = sqrt(8.0 * M_PI_ORC * q.n * CGS_MP * CGS_C * CGS_C / (6.0 * sc->beta_B * r));
+    q.nu_c = 3.0 * CGS_E * B / (4.0 * M_PI_ORC * CGS_ME * CGS_C) * q.Theta * q.Theta;
+    q.K2 = orc_bessel_k2(1.0 / q.Theta);
+    return q;
+}
+
+static void synch_coeffs_at(const synch_local *q, double nu0, double *j, double *alpha)
+{
+    double x = nu0 / q->nu_c;
+    double M = 4.0505 / pow(x, 1.0 / 6.0) * (1.0 + 0.40 / pow(x, 0.25) + 0.5316 / sqrt(x)) *
+               exp(-1.8899 * cbrt(x));
+    double jnu = nu0 * 4.0 * M_PI_ORC * q->n * CGS_E * CGS_E / (sqrt(3.0) * CGS_C * q->K2) * M;
+    /* B_nu(T) = (2 h nu^3 / c^2) / (exp(h nu / k T) - 1), k T = Theta m_e c^2 */
+    double Bnu = 2.0 * CGS_H * nu0 * nu0 * nu0 / (CGS_C * CGS_C) /
+                 expm1(CGS_H * nu0 / (q->Theta * CGS_ME * CGS_C * CGS_C));
+    *j = jnu / (4.0 * M_PI_ORC);
+    *alpha = *j / Bnu;
+}
+
+void orc_synch_coeffs(const orc_scene *sc, double r, double cost, double nu0, double *j,
+                      double *alpha)
+{
+    synch_local q = synch_at(sc, r, cost);
+    synch_coeffs_at(&q, nu0, j, alpha);
+}
+
 /* reading: torus velocity field.  Keplerian Omega(r) at BL radius r where r >= r_ISCO
  * and the orbit is timelike at (r, theta); the zero-angular-momentum observer
  * Omega = 2 a r / A elsewhere.  u^t from u.u = -1 with the metric of Eq. 1. */
@@ -348,6 +463,20 @@ static void derivs(const ray_ctx *rc, int n, const double *y, double *dy)
     double ut, Omega;
     torus_flow(rc->a, rc->r_isco, r, sint, cost, &ut, &Omega);
     double g = 1.0 / (ut * (1.0 - Omega * rc->L)); /* Eq. 2 */
+    if (sc->emitter == ORC_EMIT_SYNCH) {
+        /* lengths in r_g: d/ds per r_g of path = (per cm) * r_g */
+        double rg = orc_r_g(sc->mass);
+        synch_local q;
+        if (r <= sc->r_out) q = synch_at(sc, r, cost);
+        for (int k = 0; k < rc->n_rt; ++k) {
+            double nu0 = sc->freqs[k] / g, jnu = 0.0, anu = 0.0;
+            if (r <= sc->r_out) synch_coeffs_at(&q, nu0, &jnu, &anu);
+            double tau = y[N_GEO + 2 * k];
+            dy[N_GEO + 2 * k] = anu * rg / g;                                    /* Eq. 30 */
+            dy[N_GEO + 2 * k + 1] = jnu / (nu0 * nu0 * nu0) * rg / g * exp(-tau); /* Eq. 31 */
+        }
+        return;
+    }
     double w = sc->theta_width;
     double ne = pow(r, -sc->ne_index) * exp(-cost * cost / (2.0 * w * w));
     double Te = sc->T0 * pow(r, -sc->T_index);
@@ -467,7 +596,10 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
     rc.sgn = (sc->convention == ORC_CONV_LITERAL) ? 1.0 : -1.0;
     rc.r_isco = orc_isco(sc->a);
     rc.r_horizon = orc_horizon(sc->a);
-    rc.n_rt = (sc->emitter == ORC_EMIT_TORUS || sc->emitter == ORC_EMIT_CONST) ? sc->n_freq : 0;
+    rc.n_rt = (sc->emitter == ORC_EMIT_TORUS || sc->emitter == ORC_EMIT_CONST ||
+               sc->emitter == ORC_EMIT_SYNCH)
+                  ? sc->n_freq
+                  : 0;
     rc.n = N_GEO + 2 * rc.n_rt;
 
     double y[N_MAX], Q0, L;

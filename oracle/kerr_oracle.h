@@ -8,7 +8,13 @@
  * the CUDA library; the two sides meet only through the scene numbers a caller
  * passes to each.
  *
- * Units: G = c = M = 1 (Section 2).  The traced photon has E = 1.
+ * Units: G = c = M = 1 (Section 2).  The traced photon has E = 1.  The synchrotron shell
+ * (Section 4.5) evaluates its coefficients in CGS and scales path lengths by r_g.
+ *
+ * Pins of the synchrotron shell (tests/test_oracle_synch.py): K_2 against a library Bessel
+ * routine; the emissivity's frequency integral against the synchrotron power of a
+ * Maxwell-Juttner gas (Thomson cross-section, to the fit's few per cent); Kirchhoff's law;
+ * the optically thick limit of an isothermal shell (Rayleigh-Jeans intensity, redshifted).
  */
 #ifndef KERR_ORACLE_H
 #define KERR_ORACLE_H
@@ -31,6 +37,7 @@
 #define ORC_EMIT_TORUS 2     /* analytic thermal torus, RT Eqs. 30-31           */
 #define ORC_EMIT_CONST 3     /* test medium: dtau/ds = kappa, dI/ds = eps e^-tau */
 #define ORC_EMIT_NT_DISK 4   /* Novikov-Thorne disk: blackbody at T0 (8 pi F / 3)^1/4 */
+#define ORC_EMIT_SYNCH 5     /* Keplerian shell, thermal synchrotron (Section 4.5, CGS) */
 
 /* sign conventions for the traced photon (see the direction reading in the design notes) */
 #define ORC_CONV_PHYSICAL 0 /* real outgoing photon, traced back in affine time */
@@ -51,6 +58,10 @@ typedef struct {
     double rtol, h0, hmax_frac, horizon_factor;
     int32_t max_steps;
     int32_t convention;
+    /* synchrotron shell: n_e = n_e0 r^-ne_index exp(-cos^2/(2 w^2)) [cm^-3],
+     * Theta_e = T0 r^-T_index, B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r) [G], black-hole mass
+     * [solar masses] (lengths in r_g = G M / c^2), freqs in Hz, emission for r <= r_out */
+    double n_e0, beta_B, mass;
 } orc_scene;
 
 typedef struct {
@@ -81,6 +92,13 @@ double orc_nt_flux(double a, double r);
  * normalisation of the photon does not enter; Bardeen, Press & Teukolsky 1972). */
 double orc_circ_E(double a, double r);
 double orc_circ_L(double a, double r);
+/* Thermal synchrotron (Section 4.5): K_2 by quadrature of its integral definition, the
+ * gravitational radius in cm, and the emission / absorption coefficients in the fluid frame
+ * (CGS; j per steradian) at BL position (r, cos theta) and local frequency nu0 [Hz]. */
+double orc_bessel_k2(double x);
+double orc_r_g(double mass);
+void orc_synch_coeffs(const orc_scene *sc, double r, double cost, double nu0, double *j,
+                      double *alpha);
 double orc_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
                       double r_outer);
 int orc_trace_ray(const orc_scene *sc, double alpha, double beta, orc_result *out);

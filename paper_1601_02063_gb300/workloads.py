@@ -29,6 +29,8 @@ _DEFAULTS = dict(
     convention="physical", precision="fp64",
     # reduced-precision controls (ignored by the FP64 path)
     rtol_fp32=1e-6, r_switch=0.0,
+    # synchrotron shell: n_e at r = 1 [cm^-3], field parameter beta_B, mass [M_sun]
+    n_e0=3e7, beta_B=10.0, mass=4e6,
 )
 
 
@@ -85,6 +87,19 @@ def nt_disk(r_out: float = 20.0, n: int = 512, precision: str = "mixed") -> dict
     return scene(a=0.999, theta_obs=math.radians(85.0), alpha_min=-w, alpha_max=w, beta_min=-w,
                  beta_max=w, n_alpha=n, n_beta=n, emitter="nt_disk", r_out=r_out, T0=1.0,
                  freqs=freqs, precision=precision)
+
+
+def synch_shell(a: float = 0.0, n: int = 256, precision: str = "mixed",
+                freqs=(150e9, 340e9, 1000e9)) -> dict:
+    """Keplerian shell with thermal synchrotron emission (Section 4.5) around a 4e6 M_sun
+    black hole seen at i = 60 deg: n_e = 3e7 r^-1.1 cm^-3, Theta_e = 100 r^-0.84, field from
+    B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r) with beta_B = 10, shell out to 500 M, images
+    at 150, 340 and 1000 GHz over +-15 M (optical depth through the shell about 6, 1 and
+    0.1)."""
+    return scene(a=a, theta_obs=math.radians(60.0), alpha_min=-15.0, alpha_max=15.0,
+                 beta_min=-15.0, beta_max=15.0, n_alpha=n, n_beta=n, emitter="synch",
+                 freqs=list(freqs), r_out=500.0, ne_index=1.1, theta_width=10.0, T0=100.0,
+                 T_index=0.84, n_e0=3e7, beta_B=10.0, mass=4e6, precision=precision)
 
 
 def sweep_64(seed: int = SEED, precision: str = "mixed") -> list[dict]:
