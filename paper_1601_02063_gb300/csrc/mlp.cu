@@ -62,13 +62,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// d silu(z) / dz = s (1 + z (1 - s)), s = 1 / (1 + e^-z)
-__device__ __forceinline__ float dsilu(float z)
-{
-    const float s = 1.f / (1.f + __expf(-z));
-    return s * (1.f + z * (1.f - s));
-}
-
 }  // namespace
 
 struct odx_mlp {
@@ -81,7 +74,8 @@ struct odx_mlp {
     int64_t step = 0;
     bf16 *Z[5] = {}, *H[5] = {};  // layers 1..4
     bf16 *dZ[5] = {};             // dL/dZ_l, layers 1..4 (backward)
-    float *Y = nullptr, *dY = nullptr, *loss = nullptr;
+    float *dY = nullptr, *loss = nullptr;
+    float *loss_part = nullptr, *col_part = nullptr;  // per-block loss and column partials
     float *xin = nullptr;   // padded input rows for inference
     bf16 *wpack = nullptr;   // hidden-layer weights as forward tensor-core operands (W^T)
     bf16 *wpackB = nullptr;  // ... and as backward operands (W)
@@ -106,118 +100,6 @@ namespace {
     } while (0)
 
 __device__ __forceinline__ float bfv(const bf16 *p, int64_t i) { return __bfloat162float(p[i]); }
-
-// ---- layer 5 (256 -> 4) and the gradients of the 4-wide layers on CUDA cores ---------------
-// weights from the BF16 copy, biases from the FP32 master (added in the FP32 epilogue)
-// One warp per sample row: y = H4 . W5 + b5 (lane-strided dot products, warp reduction);
-// with targets: loss and dL/dy (1/B folded in).
-__global__ void layer5_fwd_loss(const bf16 *__restrict__ H4, const bf16 *__restrict__ pb,
-                                const float *__restrict__ p, int64_t B, int64_t B_true, float *Y,
-                                const float *__restrict__ t, float *dY, float *loss)
-{
-    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= B) return;
-    float y[NOUT] = {0.f, 0.f, 0.f, 0.f};
-    for (int n = lane; n < HID; n += 32) {
-        const float h = bfv(H4, b * HID + n);
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o) y[o] += h * bfv(pb, OFF_W5 + n * NOUT + o);
-    }
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o) {
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) y[o] += __shfl_xor_sync(0xffffffffu, y[o], s);
-        y[o] += p[OFF_B5 + o];
-    }
-    if (lane == 0) {
-        if (Y) {
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) Y[b * NOUT + o] = y[o];
-        }
-        if (t) {
-            const float *tb = t + b * 8;
-            const float c = tb[0], mx = tb[4], mg = tb[5];
-            const float inv = (b < B_true) ? 1.f / (float)B_true : 0.f;
-            const float sp = fmaxf(y[0], 0.f) - c * y[0] + log1pf(__expf(-fabsf(y[0])));
-            const float e1 = y[1] - tb[1], e2 = y[2] - tb[2], e3 = y[3] - tb[3];
-            const float l = sp + mx * (e1 * e1 + e2 * e2) + mg * e3 * e3;
-            dY[b * NOUT + 0] = inv * (1.f / (1.f + __expf(-y[0])) - c);
-            dY[b * NOUT + 1] = inv * 2.f * mx * e1;
-            dY[b * NOUT + 2] = inv * 2.f * mx * e2;
-            dY[b * NOUT + 3] = inv * 2.f * mg * e3;
-            if (b < B_true) atomicAdd(loss, l * inv);
-        }
-    }
-}
-
-// dZ4 = (dY W5^T) * silu'(Z4), one thread per (b, n).
-__global__ void layer5_bwd_dz(const float *__restrict__ dY, const bf16 *__restrict__ pb,
-                              const bf16 *__restrict__ Z4, int64_t B, bf16 *dZ4)
-{
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= B * HID) return;
-    const int64_t b = idx / HID;
-    const int n = (int)(idx % HID);
-    float v = 0.f;
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o) v += dY[b * NOUT + o] * bfv(pb, OFF_W5 + n * NOUT + o);
-    dZ4[idx] = __float2bfloat16_rn(v * dsilu(__bfloat162float(Z4[idx])));
-}
-
-// Column reductions over a chunk of 256 rows per block, thread n:
-//   g_out[n][o] += sum_b Hin[b][n] * dY[b][o]  (dW5) and g_b[o] += sum_b dY[b][o] (db5)
-__global__ void layer5_bwd_w(const bf16 *__restrict__ H4, const float *__restrict__ dY, int64_t B,
-                             float *gW5, float *gb5)
-{
-    const int n = threadIdx.x;  // 256 threads
-    const int64_t b0 = (int64_t)blockIdx.x * 256;
-    __shared__ float sdy[256][NOUT];
-    for (int i = n; i < 256 * NOUT; i += 256) {
-        const int64_t b = b0 + i / NOUT;
-        sdy[i / NOUT][i % NOUT] = (b < B) ? dY[b * NOUT + i % NOUT] : 0.f;
-    }
-    __syncthreads();
-    float acc[NOUT] = {0.f, 0.f, 0.f, 0.f};
-    for (int r = 0; r < 256 && b0 + r < B; ++r) {
-        const float h = bfv(H4, (b0 + r) * HID + n);
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o) acc[o] += h * sdy[r][o];
-    }
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o) atomicAdd(&gW5[n * NOUT + o], acc[o]);
-    if (n < NOUT) {
-        float s = 0.f;
-        for (int r = 0; r < 256 && b0 + r < B; ++r) s += sdy[r][n];
-        atomicAdd(&gb5[n], s);
-    }
-}
-
-// Bias gradient of a hidden layer: gb[n] += sum_b dZ[b][n] (256 rows per block).
-__global__ void bias_grad(const bf16 *__restrict__ dZ, int64_t B, float *gb)
-{
-    const int n = threadIdx.x;
-    const int64_t b0 = (int64_t)blockIdx.x * 256;
-    float s = 0.f;
-    for (int r = 0; r < 256 && b0 + r < B; ++r) s += bfv(dZ, (b0 + r) * HID + n);
-    atomicAdd(&gb[n], s);
-}
-
-// Layer-1 weight gradient: gW1[k][n] += sum_b x[b][k] dZ1[b][n].
-__global__ void layer1_bwd_w(const float *__restrict__ x, const bf16 *__restrict__ dZ1, int64_t B,
-                             float *gW1)
-{
-    const int n = threadIdx.x;
-    const int64_t b0 = (int64_t)blockIdx.x * 256;
-    float acc[NIN] = {0.f, 0.f, 0.f, 0.f};
-    for (int r = 0; r < 256 && b0 + r < B; ++r) {
-        const float d = bfv(dZ1, (b0 + r) * HID + n);
-#pragma unroll
-        for (int k = 0; k < NIN; ++k) acc[k] += x[(b0 + r) * NIN + k] * d;
-    }
-#pragma unroll
-    for (int k = 0; k < NIN; ++k) atomicAdd(&gW1[k * HID + n], acc[k]);
-}
 
 // Adam (Kingma & Ba 2015) on the FP32 master weights; refreshes the BF16 copy.
 __global__ void adam_step(float *p, bf16 *pb, const float *g, float *m1, float *m2, int n,
@@ -811,6 +693,197 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
     if (warp == 0) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
 }
 
+// ---- layer 5 (256 -> 4), the loss and the column reductions on CUDA cores -----------------
+// Weights from the BF16 copy, biases from the FP32 master.  One warp per sample row, lane l
+// holding columns 8 l .. 8 l + 7 (one 16-byte load of H4 and of Z4 covers the row):
+//   y = H4 W5 + b5; loss = softplus(y0) - c y0 + m_x (e1^2 + e2^2) + m_g e3^2 with
+//   e_k = y_k - t_k (mean over the batch); dL/dy; dL/dZ4 = (dL/dy W5^T) silu'(Z4)
+// (sigmoid and silu' in the tanh form the tensor-core chain uses).
+// Each block writes its loss partial; grad_finish adds them in block order.
+constexpr int L5_THREADS = 256, L5_BLOCKS = 1024;
+
+__global__ void __launch_bounds__(L5_THREADS, 3) layer5_fused(
+    const bf16 *__restrict__ H4, const bf16 *__restrict__ Z4, const bf16 *__restrict__ pb,
+    const float *__restrict__ p, int64_t B, const float *__restrict__ t, float *__restrict__ dY,
+    bf16 *__restrict__ dZ4, float *__restrict__ loss_part)
+{
+    __shared__ float sl[L5_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float w[8][NOUT], b5[NOUT];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) w[j][o] = bfv(pb, OFF_W5 + (8 * lane + j) * NOUT + o);
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) b5[o] = p[OFF_B5 + o];
+    const float inv = 1.f / (float)B;
+    float lsum = 0.f;
+    const int64_t wstride = (int64_t)gridDim.x * (L5_THREADS / 32);
+    for (int64_t b = (int64_t)blockIdx.x * (L5_THREADS / 32) + warp; b < B; b += wstride) {
+        float h[8], z[8];
+        unpack8(*reinterpret_cast<const uint4 *>(H4 + b * HID + 8 * lane), h);
+        unpack8(*reinterpret_cast<const uint4 *>(Z4 + b * HID + 8 * lane), z);
+        float y[NOUT] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) y[o] = fmaf(h[j], w[j][o], y[o]);
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) y[o] += __shfl_xor_sync(0xffffffffu, y[o], s);
+            y[o] += b5[o];
+        }
+        const float4 t0 = *reinterpret_cast<const float4 *>(t + b * 8);
+        const float4 t1 = *reinterpret_cast<const float4 *>(t + b * 8 + 4);
+        const float c = t0.x, mx = t1.x, mg = t1.y;
+        const float e1 = y[1] - t0.y, e2 = y[2] - t0.z, e3 = y[3] - t0.w;
+        const float sg = fmaf(0.5f, tanh_fast(0.5f * y[0]), 0.5f);  // sigmoid(y0)
+        const float d[NOUT] = {inv * (sg - c), inv * 2.f * mx * e1,
+                               inv * 2.f * mx * e2, inv * 2.f * mg * e3};
+        if (lane == 0) {
+            const float sp = fmaxf(y[0], 0.f) - c * y[0] + log1pf(__expf(-fabsf(y[0])));
+            lsum += inv * (sp + mx * (e1 * e1 + e2 * e2) + mg * e3 * e3);
+            *reinterpret_cast<float4 *>(dY + b * NOUT) = make_float4(d[0], d[1], d[2], d[3]);
+        }
+        float dz[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) v = fmaf(d[o], w[j][o], v);
+            dz[j] = v * dsilu_fast(z[j]);
+        }
+        *reinterpret_cast<uint4 *>(dZ4 + b * HID + 8 * lane) = pack8(dz);
+    }
+    if (lane == 0) sl[warp] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = 0.f;
+        for (int i = 0; i < L5_THREADS / 32; ++i) v += sl[i];
+        loss_part[blockIdx.x] = v;
+    }
+}
+
+// Batch sums for the bias and the 4-wide weight gradients, one job per blockIdx.y:
+//   jobs 0-2: gb_l[n] = sum_b dZ_l[b][n]                (l = 4, 3, 2)
+//   job 3:    gb_1[n] = sum_b dZ_1[b][n], gW1[k][n] = sum_b x[b][k] dZ_1[b][n]
+//   job 4:    gW5[n][o] = sum_b H4[b][n] dY[b][o],     gb5[o] = sum_b dY[b][o]
+// A block takes a contiguous run of rows; thread (row phase r, column group g) adds every
+// 8th row of columns 8 g .. 8 g + 7, the 8 phases are then added in order through shared
+// memory, and the block writes part[job][block][k][n] (k: the CR_K weighted sums).
+constexpr int CR_THREADS = 256, CR_BLOCKS = 128, CR_K = 5, CR_JOBS = 5;
+
+struct ColArgs {
+    const bf16 *A[CR_JOBS];  // dZ4, dZ3, dZ2, dZ1, H4
+    const float *x, *dY;
+    int64_t B;
+    float *part;  // [CR_JOBS][CR_BLOCKS][CR_K][HID]
+};
+
+template <int JOB>
+__device__ __forceinline__ void col_rows(const ColArgs &C, int64_t r0, int64_t r1, int rp, int g,
+                                         float (&acc)[CR_K][8])
+{
+    const bf16 *A = C.A[JOB];
+#pragma unroll 4
+    for (int64_t b = r0 + rp; b < r1; b += 8) {
+        float a[8];
+        unpack8(*reinterpret_cast<const uint4 *>(A + b * HID + 8 * g), a);
+        if constexpr (JOB < 3) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[0][j] += a[j];
+        } else if constexpr (JOB == 3) {
+            const float4 xv = *reinterpret_cast<const float4 *>(C.x + b * NIN);
+            const float wk[NIN] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                acc[0][j] += a[j];
+#pragma unroll
+                for (int k = 0; k < NIN; ++k) acc[1 + k][j] = fmaf(wk[k], a[j], acc[1 + k][j]);
+            }
+        } else {
+            const float4 dv = *reinterpret_cast<const float4 *>(C.dY + b * NOUT);
+            const float wk[NOUT] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) acc[k][j] = fmaf(wk[k], a[j], acc[k][j]);
+            if (g == 0)
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) acc[4][k] += wk[k];  // gb5 in slot (4, k)
+        }
+    }
+}
+
+__global__ void __launch_bounds__(CR_THREADS) col_reduce(const __grid_constant__ ColArgs C)
+{
+    __shared__ float sh[8][HID];
+    const int job = blockIdx.y, g = threadIdx.x & 31, rp = threadIdx.x >> 5;
+    const int64_t r0 = C.B * blockIdx.x / gridDim.x, r1 = C.B * (blockIdx.x + 1) / gridDim.x;
+    float acc[CR_K][8];
+#pragma unroll
+    for (int k = 0; k < CR_K; ++k)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
+    switch (job) {
+    case 0: col_rows<0>(C, r0, r1, rp, g, acc); break;
+    case 1: col_rows<1>(C, r0, r1, rp, g, acc); break;
+    case 2: col_rows<2>(C, r0, r1, rp, g, acc); break;
+    case 3: col_rows<3>(C, r0, r1, rp, g, acc); break;
+    default: col_rows<4>(C, r0, r1, rp, g, acc); break;
+    }
+    float *out = C.part + ((size_t)job * gridDim.x + blockIdx.x) * CR_K * HID;
+#pragma unroll
+    for (int k = 0; k < CR_K; ++k) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sh[rp][8 * g + j] = acc[k][j];
+        __syncthreads();
+        const int n = threadIdx.x;
+        float v = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v += sh[q][n];
+        out[k * HID + n] = v;
+        __syncthreads();
+    }
+}
+
+// Gradients of the biases and the 4-wide layers, and the loss, one warp per output: lane l
+// adds partials l, l + 32, ... in order, then a fixed shuffle tree.  Outputs, in warp order:
+// gb_4, gb_3, gb_2 (3 x 256), gb_1 and gW1 (5 x 256), gW5 (4 x 256), gb5 (4), the loss.
+constexpr int GF_OUTPUTS = 3 * HID + 5 * HID + 4 * HID + NOUT + 1;
+
+__global__ void grad_finish(const float *__restrict__ part, const float *__restrict__ loss_part,
+                            float *__restrict__ grad, float *__restrict__ loss)
+{
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= GF_OUTPUTS) return;
+    int job, k, n;
+    const float *src;
+    int count, stride;
+    if (w == GF_OUTPUTS - 1) {
+        src = loss_part, count = L5_BLOCKS, stride = 1;
+        job = k = n = -1;
+    } else {
+        if (w < 3 * HID) job = w / HID, k = 0, n = w % HID;
+        else if (w < 8 * HID) job = 3, k = (w - 3 * HID) / HID, n = w % HID;
+        else if (w < 12 * HID) job = 4, k = (w - 8 * HID) / HID, n = w % HID;
+        else job = 4, k = 4, n = w - 12 * HID;
+        src = part + ((size_t)job * CR_BLOCKS * CR_K + k) * HID + n;
+        count = CR_BLOCKS, stride = CR_K * HID;
+    }
+    float v = 0.f;
+    for (int i = lane; i < count; i += 32) v += src[(size_t)i * stride];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane != 0) return;
+    if (job < 0) *loss = v;
+    else if (job < 3) grad[off_b(4 - job) + n] = v;
+    else if (job == 3) grad[k == 0 ? OFF_B1 + n : OFF_W1 + (k - 1) * HID + n] = v;
+    else if (k < NOUT) grad[OFF_W5 + n * NOUT + k] = v;
+    else grad[OFF_B5 + n] = v;
+}
+
 // ---- weight gradients on tcgen05: dW_l = H_{l-1}^T dZ_l --------------------------------------
 // The batch index is the reduction index and the row index of both operands in HBM, so both
 // are MN-major for the tensor core: a 16-byte piece of one row (8 consecutive features) is one
@@ -989,27 +1062,24 @@ TcArgs chain_args(odx_mlp *m, const bf16 *wpack, int64_t n)
 
 // Training forward over B rows (B multiple of 128) on the tensor cores, Z_l and H_l kept;
 // then layer 5 with the loss and dL/dy (targets t).
-void forward(odx_mlp *m, const float *x, int64_t B, int64_t B_true, float *Y, const float *t,
-             cudaStream_t st)
+// Training forward pass of B rows (targets t[B][8]): Z_l, H_l kept for the backward pass,
+// the loss partials, dL/dy and dL/dZ4.
+void forward(odx_mlp *m, const float *x, int64_t B, const float *t, cudaStream_t st)
 {
     pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0);
     TcArgs a = chain_args(m, m->wpack, B);
     a.x = x;
     launch_chain<TC_TRAIN>(m, a, B, st);
-    layer5_fwd_loss<<<blocks_for(B * 32, 256), 256, 0, st>>>(m->H[4], m->pb, m->p, B, B_true, Y,
-                                                             t, m->dY, m->loss);
+    layer5_fused<<<L5_BLOCKS, L5_THREADS, 0, st>>>(m->H[4], m->Z[4], m->pb, m->p, B, t, m->dY,
+                                                   m->dZ[4], m->loss_part);
 }
 
-// Backward pass after forward(): gradients into m->grad (zeroed here).  dL/dZ through the
-// three 256 x 256 layers on the tensor cores (one chain per row tile); the weight gradients
-// dW_l = H_{l-1}^T dZ_l reduce over the batch on the tensor cores too (split over the batch,
-// partials added in split order).
+// Backward pass after forward(): every gradient into m->grad, the loss into m->loss.  dL/dZ
+// through the three 256 x 256 layers on the tensor cores (one chain per row tile); the weight
+// gradients dW_l = H_{l-1}^T dZ_l reduce over the batch on the tensor cores too (split over
+// the batch, partials added in split order); bias and 4-wide-layer gradients as column sums.
 void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
 {
-    cudaMemsetAsync(m->grad, 0, NPARAM * sizeof(float), st);
-    const unsigned rblocks = blocks_for(B, 256);
-    layer5_bwd_w<<<rblocks, 256, 0, st>>>(m->H[4], m->dY, B, m->grad + OFF_W5, m->grad + OFF_B5);
-    layer5_bwd_dz<<<blocks_for(B * HID, 256), 256, 0, st>>>(m->dY, m->pb, m->Z[4], B, m->dZ[4]);
     pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpackB, 1);
     TcArgs a = chain_args(m, m->wpackB, B);
     a.dZ4 = m->dZ[4];
@@ -1026,16 +1096,23 @@ void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
     const int splits = (int)std::min<int64_t>(DW_MAX_SPLITS, dw.n_chunks);
     mlp_dw_tc<<<dim3((unsigned)splits, 3), DW_THREADS, DW_SMEM, st>>>(dw);
     dw_reduce<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->dw_part, splits, m->grad);
-    for (int l = 4; l >= 2; --l) bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[l], B, m->grad + off_b(l));
-    layer1_bwd_w<<<rblocks, 256, 0, st>>>(x, m->dZ[1], B, m->grad + OFF_W1);
-    bias_grad<<<rblocks, 256, 0, st>>>(m->dZ[1], B, m->grad + OFF_B1);
+    ColArgs c{};
+    for (int l = 4; l >= 1; --l) c.A[4 - l] = m->dZ[l];
+    c.A[4] = m->H[4];
+    c.x = x;
+    c.dY = m->dY;
+    c.B = B;
+    c.part = m->col_part;
+    col_reduce<<<dim3(CR_BLOCKS, CR_JOBS), CR_THREADS, 0, st>>>(c);
+    grad_finish<<<blocks_for((int64_t)GF_OUTPUTS * 32, 256), 256, 0, st>>>(m->col_part, m->loss_part,
+                                                                        m->grad, m->loss);
 }
 
 void free_mlp(odx_mlp *m)
 {
     cudaSetDevice(m->device);
     for (void *q : {(void *)m->p, (void *)m->pb, (void *)m->grad, (void *)m->m1, (void *)m->m2,
-                    (void *)m->Y, (void *)m->dY, (void *)m->loss, (void *)m->wpackB,
+                    (void *)m->dY, (void *)m->loss, (void *)m->loss_part, (void *)m->col_part, (void *)m->wpackB,
                     (void *)m->dw_part,
                     (void *)m->xin, (void *)m->surr_x, (void *)m->surr_y, (void *)m->fb_rays,
                     (void *)m->fb_pix, (void *)m->fb_count, (void *)m->bcrit,
@@ -1097,7 +1174,9 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
               cudaMalloc(&m->wpackB, (size_t)3 * HID * HID * sizeof(bf16)) == cudaSuccess &&
               cudaMalloc(&m->dw_part, (size_t)3 * DW_MAX_SPLITS * HID * HID * sizeof(float)) ==
                   cudaSuccess &&
-              cudaMalloc(&m->Y, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->loss_part, L5_BLOCKS * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&m->col_part, (size_t)CR_JOBS * CR_BLOCKS * CR_K * HID * sizeof(float)) ==
+                  cudaSuccess &&
               cudaMalloc(&m->dY, m->max_batch * NOUT * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->loss, sizeof(float)) == cudaSuccess &&
               cudaMalloc(&m->xin, m->max_batch * NIN * sizeof(float)) == cudaSuccess &&
@@ -1179,11 +1258,11 @@ int32_t odx_mlp_forward(odx_mlp *m, const float *x, int64_t n, float *y, void *s
 int32_t odx_mlp_gradients(odx_mlp *m, const float *x, const float *t, int64_t n, float *grad_host,
                           float *loss_host)
 {
-    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || ((uintptr_t)x & 15u))
+    if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || ((uintptr_t)x & 15u) ||
+        ((uintptr_t)t & 15u))
         return ODX_ERR_INVALID_ARG;
     MLP_CUDA(cudaSetDevice(m->device));
-    MLP_CUDA(cudaMemset(m->loss, 0, sizeof(float)));
-    forward(m, x, n, n, m->Y, t, nullptr);
+    forward(m, x, n, t, nullptr);
     backward(m, x, n, nullptr);
     MLP_CUDA(cudaDeviceSynchronize());
     if (grad_host)
@@ -1196,12 +1275,11 @@ int32_t odx_mlp_train_step(odx_mlp *m, const float *x, const float *t, int64_t n
                            float *loss_dev, void *stream)
 {
     if (!m || !x || !t || n < 1 || n > m->max_batch || n % 128 != 0 || !(lr > 0.f) ||
-        ((uintptr_t)x & 15u))
+        ((uintptr_t)x & 15u) || ((uintptr_t)t & 15u))
         return ODX_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CUDA(cudaSetDevice(m->device));
-    MLP_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
-    forward(m, x, n, n, m->Y, t, st);
+    forward(m, x, n, t, st);
     backward(m, x, n, st);
     m->step += 1;
     const float b1 = 0.9f, b2 = 0.999f;

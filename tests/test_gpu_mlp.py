@@ -125,6 +125,9 @@ def test_gradients_match_fp64_reference(tracer):
         # keep the device tensors alive for the duration of the call
         x_dev, t_dev = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
         g, loss = B.odx_mlp_gradients(s.mlp, x_dev.data_ptr(), t_dev.data_ptr(), n)
+        # batch reductions are split into fixed partials added in a fixed order
+        g2, loss2 = B.odx_mlp_gradients(s.mlp, x_dev.data_ptr(), t_dev.data_ptr(), n)
+        assert np.array_equal(g, g2) and loss == loss2
         w = _weights_as_used(flat.astype(np.float32))
         g_ref = mlp.gradients(w, x.astype(np.float64), t.astype(np.float64))
         assert abs(loss - mlp.loss(w, x.astype(np.float64), t.astype(np.float64))) < 2e-2 * loss
