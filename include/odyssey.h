@@ -56,6 +56,16 @@ extern "C" {
                                 hit emits a blackbody at T(r) = T0 (8 pi F(r) / 3)^(1/4), F the
                                 Page-Thorne flux for unit accretion rate, seen as B_nu(g T) at
                                 the n_freq observed frequencies (n_freq image planes) */
+#define ODX_EMIT_SYNCH 4     /* Keplerian shell of thermal synchrotron plasma (Section 4.5,
+                                Eqs. 37-39) with Kirchhoff absorption, transfer Eqs. 30-31 in
+                                CGS: freqs in Hz, n_freq image planes of I_nu in
+                                erg s^-1 cm^-2 Hz^-1 sr^-1; n_e = n_e0 r^-ne_index
+                                exp(-cos^2 theta / (2 theta_width^2)) cm^-3, Theta_e = k T_e /
+                                m_e c^2 = T0 r^-T_index, B^2 / 8 pi = n_e m_p c^2 /
+                                (6 beta_B r), emission for r <= r_out, lengths in
+                                r_g = G mass / c^2; the flow is the torus's.  The printed
+                                emissivity integrates over directions: the transfer uses
+                                j_nu / 4 pi per steradian */
 
 /* arithmetic of the integrator */
 #define ODX_FP64 0  /* every stage in FP64                                             */
@@ -94,6 +104,9 @@ typedef struct odx_scene {
     int32_t reserved;               /* must be 0                                         */
     double rtol_fp32;               /* ODX_MIXED: relative tolerance of the FP32 stages  */
     double r_switch;                /* ODX_MIXED: FP64 stages where r < r_switch         */
+    double n_e0;                    /* synchrotron shell: n_e at r = 1 (cm^-3), > 0      */
+    double beta_B;                  /* synchrotron shell: field parameter, > 0           */
+    double mass;                    /* synchrotron shell: black-hole mass (M_sun), > 0   */
 } odx_scene;
 
 /*
@@ -300,7 +313,7 @@ int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Ad
 int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
 /* Training rows: x_dev[n][4] = (alpha / 20, beta / 20, a, cos i), 16-byte aligned;
  * t_dev[n][8] as written by odx_mlp_targets (captured flag, log r_cross, phi_cross / pi, g,
- * crossing mask, g mask, 0, 0).  Both device pointers, caller-owned.
+ * crossing mask, g mask, 0, 0), 16-byte aligned.  Both device pointers, caller-owned.
  * Loss and gradients (dL/dparams, layout as the parameters) of one batch, n a multiple of
  * 128 and <= max_batch; synchronous, results copied to host (either may be NULL); returns
  * ODX_ERR_DEVICE_FLAG if a tensor-core wait timed out in this or an earlier call. */

@@ -219,4 +219,37 @@ __device__ __forceinline__ double carter_q(double a, double L, const double y[6]
     return y[5] * y[5] + (L * L / (s * s) - a * a) * c * c;
 }
 
+// ---- thermal synchrotron shell (Section 4.5) ---------------------------------------------
+// CGS constants (CODATA 2018; G M_sun the IAU nominal value).
+constexpr double kCgsC = 2.99792458e10, kCgsE = 4.803204712570263e-10, kCgsMe = 9.1093837015e-28,
+                 kCgsMp = 1.67262192369e-24, kCgsH = 6.62607015e-27, kCgsGMsun = 1.3271244e26;
+// The stages take frequencies in GHz and carry I-hat = (I_nu / nu^3) / Aj.
+constexpr double kNuUnit = 1e9;
+
+struct SynchK {
+    double inv_kc;  // 1 / nu_c-hat at r = 1, n_e = n_e0, Theta_e = 1 (nu_c in GHz)
+    double ky;      // h nu / k T_e = ky nu-hat / Theta_e
+    double Atau;    // dtau/ds = Atau * (dI-hat/ds without exp(-tau)) * expm1(h nu0 / k T_e)
+    double Aj;      // I_nu / nu^3 = Aj * I-hat (CGS, nu in Hz)
+};
+
+// With nr = n_e / n_e0, per unit path in r_g and nu0-hat the fluid-frame frequency in GHz:
+//   j_nu / 4 pi = nu0 n_e e^2 / (sqrt(3) c K_2(1/Theta_e)) M(x_M)            (Eq. 37)
+//   nu_c = 3 e B / (4 pi m_e c) Theta_e^2, B = B0 sqrt(nr / r)                (Eq. 39)
+//   dI/ds = r_g j_nu / (4 pi g nu0^3) exp(-tau) = Aj nr M / (K_2 nu0-hat^2 g) exp(-tau)
+//   dtau/ds = r_g alpha_nu / g = (c^2 / 2 h) expm1(h nu0 / k T_e) * (the same without exp)
+// B0 = sqrt(8 pi n_e0 m_p c^2 / (6 beta_B)) from B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r).
+__host__ __device__ inline SynchK synch_constants(const odx_scene &s)
+{
+    const double pi = 3.14159265358979323846;
+    const double rg = kCgsGMsun * s.mass / (kCgsC * kCgsC);
+    const double B0 = sqrt(8.0 * pi * s.n_e0 * kCgsMp * kCgsC * kCgsC / (6.0 * s.beta_B));
+    SynchK k;
+    k.inv_kc = 4.0 * pi * kCgsMe * kCgsC * kNuUnit / (3.0 * kCgsE * B0);
+    k.ky = kCgsH * kNuUnit / (kCgsMe * kCgsC * kCgsC);
+    k.Aj = kCgsE * kCgsE * s.n_e0 * rg / (sqrt(3.0) * kCgsC * kNuUnit * kNuUnit);
+    k.Atau = k.Aj * kCgsC * kCgsC / (2.0 * kCgsH);
+    return k;
+}
+
 }  // namespace odx

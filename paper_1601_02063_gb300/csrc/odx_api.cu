@@ -89,14 +89,15 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
         if (s.n_alpha < 1 || s.n_beta < 1)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
     }
-    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_NT_DISK)
+    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_SYNCH)
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown emitter %d", k, s.emitter);
     if (odx::disk_emitter(s.emitter) &&
         (!finite(s.r_in) || !finite(s.r_out) || !(s.r_out > 0.0) || !finite(s.q_emis)))
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad thin-disk parameters", k);
     if (s.emitter == ODX_EMIT_NT_DISK && (!(s.T0 > 0.0) || !finite(s.T0)))
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: NT disk needs T0 > 0", k);
-    if (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK) {
+    if (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK ||
+        s.emitter == ODX_EMIT_SYNCH) {
         if (s.n_freq < 1 || s.n_freq > ODX_MAX_FREQ)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: n_freq must be 1..%d", k, ODX_MAX_FREQ);
         for (int f = 0; f < s.n_freq; ++f)
@@ -107,6 +108,13 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
         if (!finite(s.C_norm) || s.C_norm < 0.0 || !(s.theta_width > 0.0) || !(s.T0 > 0.0) ||
             !finite(s.ne_index) || !finite(s.T_index) || !finite(s.theta_width) || !finite(s.T0))
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad torus parameters", k);
+    }
+    if (s.emitter == ODX_EMIT_SYNCH) {
+        if (!(s.n_e0 > 0.0) || !finite(s.n_e0) || !(s.beta_B > 0.0) || !finite(s.beta_B) ||
+            !(s.mass > 0.0) || !finite(s.mass) || !(s.T0 > 0.0) || !finite(s.T0) ||
+            !(s.theta_width > 0.0) || !finite(s.theta_width) || !finite(s.ne_index) ||
+            !finite(s.T_index) || !finite(s.r_out) || !(s.r_out > 0.0))
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad synchrotron-shell parameters", k);
     }
     if (!(s.rtol > 0.0) || !finite(s.rtol) || !(s.h0 > 0.0) || !finite(s.h0) ||
         !(s.hmax_frac > 0.0) || !finite(s.hmax_frac) || !(s.horizon_factor > 1.0) ||
@@ -126,7 +134,7 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
 // Compiled transfer slots: 3 (the three-frequency workloads), 4 or 8.
 int32_t nf_slots(int32_t emitter, int32_t n_freq)
 {
-    if (emitter != ODX_EMIT_TORUS) return 0;
+    if (emitter != ODX_EMIT_TORUS && emitter != ODX_EMIT_SYNCH) return 0;
     return n_freq <= 3 ? 3 : (n_freq <= 4 ? 4 : 8);
 }
 
@@ -323,9 +331,24 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
     d.f_lr_pref = (float)(0.5 * s.T_index - 2.0 * s.ne_index);
     d.f_c2_pref = torus ? (float)(-1.0 / (s.theta_width * s.theta_width)) : 0.f;
     d.f_pref0 = torus ? (float)(s.C_norm / sqrt(s.T0)) : 0.f;
+    // synchrotron shell (Section 4.5): n_e / n_e0 = r^-ne_index exp(-cos^2 / (2 w^2)),
+    // 1 / Theta_e = r^T_index / T0, frequencies in GHz
+    const bool synch = s.emitter == ODX_EMIT_SYNCH && s.T0 > 0.0 && s.theta_width > 0.0 &&
+                       s.n_e0 > 0.0 && s.beta_B > 0.0 && s.mass > 0.0;
+    if (synch) {
+        const SynchK q = synch_constants(s);
+        d.f_synch = 1;
+        d.f_inv_T0 = (float)(1.0 / s.T0);
+        d.f_lr_pref = (float)(-s.ne_index);
+        d.f_c2_pref = (float)(-1.0 / (2.0 * s.theta_width * s.theta_width));
+        d.f_inv_kc = (float)q.inv_kc;
+        d.f_ky = (float)q.ky;
+        d.f_Atau = (float)q.Atau;
+    }
+    const double nu_scale = synch ? 1.0 / kNuUnit : 1.0;
     const int nf = (s.n_freq > 0 && s.n_freq <= ODX_MAX_FREQ) ? s.n_freq : 0;
     for (int k = 0; k < ODX_MAX_FREQ; ++k) {
-        const double nu = nf > 0 ? s.freqs[k < nf ? k : nf - 1] : 1.0;
+        const double nu = nf > 0 ? s.freqs[k < nf ? k : nf - 1] * nu_scale : 1.0;
         d.f_nu[k] = (float)nu;
         d.f_inv_nu3[k] = (nu > 0.0) ? (float)(1.0 / (nu * nu * nu)) : 0.f;
     }
@@ -343,6 +366,11 @@ void set_launch_medium(TraceArgs &a, const DevScene &d, bool single)
         a.med.nu[k] = d.f_nu[k];
         a.med.inv_nu3[k] = d.f_inv_nu3[k];
     }
+    a.med.inv_kc = d.f_inv_kc;
+    a.med.ky = d.f_ky;
+    a.med.Atau = d.f_Atau;
+    a.med.r_out = d.f_r_out;
+    a.med.synch = d.f_synch;
 }
 
 // Argument checks of odx_render for callers without a context (no message is stored).

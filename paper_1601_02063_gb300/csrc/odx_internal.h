@@ -9,11 +9,14 @@
 
 namespace odx {
 
-// Image planes of a scene: one per observed frequency for the torus and the Novikov-Thorne
-// disk, otherwise one (thin-disk intensity, or zero for geodesics only).
+// Image planes of a scene: one per observed frequency for the torus, the Novikov-Thorne disk
+// and the synchrotron shell, otherwise one (thin-disk intensity, or zero for geodesics only).
 __host__ __device__ inline int32_t scene_planes(const odx_scene &s)
 {
-    return (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK) ? s.n_freq : 1;
+    return (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK ||
+            s.emitter == ODX_EMIT_SYNCH)
+               ? s.n_freq
+               : 1;
 }
 // Emitters whose rays stop on the opaque equatorial disk r_in <= r <= r_out.
 __host__ __device__ inline bool disk_emitter(int32_t e)
@@ -40,7 +43,12 @@ struct DevScene {
     float f_c2_pref;
     float f_pref0;
     float f_nu[ODX_MAX_FREQ];       // observed frequencies, padded past n_freq with the last
+                                    // (synchrotron shell: in GHz)
     float f_inv_nu3[ODX_MAX_FREQ];  // 1 / f_nu^3
+    // synchrotron shell (f_synch = 1): n_e / n_e0 = exp(f_lr_pref ln r + f_c2_pref cos^2),
+    // 1 / Theta_e from f_T_index, f_inv_T0 as for the torus; SynchK in FP32
+    float f_inv_kc, f_ky, f_Atau;
+    int32_t f_synch;
 };
 
 // One scene-table entry for a scene whose rays start at ray_begin (all table builders).
@@ -59,6 +67,8 @@ struct DevStats {
 struct MedConst {
     float T_index, inv_T0, lr_pref, c2_pref, pref0;
     float nu[ODX_MAX_FREQ], inv_nu3[ODX_MAX_FREQ];
+    float inv_kc, ky, Atau, r_out;
+    int32_t synch;
 };
 
 struct TraceArgs {

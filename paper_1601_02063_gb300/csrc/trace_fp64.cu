@@ -103,11 +103,13 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     store_record(A.records + R.id, o);
     if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
         if constexpr (NF > 0) {
+            // synchrotron shell: the stages carry I_nu / (nu^3 Aj), nu in Hz
+            const double Ij = S.s.emitter == ODX_EMIT_SYNCH ? synch_constants(S.s).Aj : 1.0;
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
                 if (k < S.s.n_freq) {
                     const double nu = S.s.freqs[k];
-                    img[(int64_t)k * S.n_rays] = nu * nu * nu * R.I[k];
+                    img[(int64_t)k * S.n_rays] = nu * nu * nu * Ij * R.I[k];
                 }
             }
         } else {

@@ -263,6 +263,8 @@ template <int NF>
 struct MediumF {
     float T_index, inv_T0, lr_pref, c2_pref, pref0;
     float nu[NF + 1], inv_nu3[NF + 1];
+    float inv_kc, ky, Atau, r_out;  // synchrotron shell
+    int32_t synch;
 };
 
 template <int NF>
@@ -279,7 +281,32 @@ __device__ __forceinline__ MediumF<NF> medium_f(const DevScene &S)
         m.nu[k] = S.f_nu[k < ODX_MAX_FREQ ? k : 0];
         m.inv_nu3[k] = S.f_inv_nu3[k < ODX_MAX_FREQ ? k : 0];
     }
+    m.inv_kc = S.f_inv_kc;
+    m.ky = S.f_ky;
+    m.Atau = S.f_Atau;
+    m.r_out = S.f_r_out;
+    m.synch = S.f_synch;
     return m;
+}
+
+// FP32 transfer terms of the synchrotron shell (Eqs. 30-31 with Eqs. 37-39; the FP64 form
+// is synch_rhs): nr = n_e / n_e0, iTh = 1 / Theta_e, ig = 1 / g.
+template <int NF, class Med>
+__device__ __forceinline__ void synch32(const Med &m, float r, float nr, float iTh, float ig,
+                                        const float *tau, float *ft, float *fI)
+{
+    const float P = nr * ig * __frcp_rn(k2_scaled<float>(iTh));
+    const float inu_c = m.inv_kc * iTh * iTh * sqrtf(r * __frcp_rn(nr));
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        const float nu0 = m.nu[k] * ig;
+        const float w = __expf(__logf(nu0 * inu_c) * (-1.f / 12.f));  // x^-1/12
+        const float w2 = w * w, w3 = w2 * w, w6 = w3 * w3;
+        const float Mp = 4.0505f * w2 * (1.f + 0.40f * w3 + 0.5316f * w6);
+        const float jt = P * Mp * __expf(iTh - 1.8899f * __frcp_rn(w2 * w2)) * __frcp_rn(nu0 * nu0);
+        ft[k] = m.Atau * jt * expm1f(m.ky * nu0 * iTh);  // Eq. 30, Kirchhoff
+        fI[k] = jt * __expf(-tau[k]);                     // Eq. 31
+    }
 }
 
 // Hardware reciprocal (relative error ~1 ulp; the FP32 stages run at rtol ~1e-6).
@@ -413,8 +440,18 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, floa
             N = -Sig * Del * iA;
         }
         const float ig = (1.f - Om * L) * rsqrtf(-N);
-        const float gg = rcp_fast(ig);
         const float lr = __logf(r);
+        if (m.synch) {
+            if (r <= m.r_out) {
+                const float nr = __expf(m.lr_pref * lr + m.c2_pref * c * c);
+                synch32<NF>(m, r, nr, m.inv_T0 * __expf(m.T_index * lr), ig, in + 4, ft, fI);
+            } else {
+#pragma unroll
+                for (int k = 0; k < NF; ++k) ft[k] = fI[k] = 0.f;
+            }
+            return;
+        }
+        const float gg = rcp_fast(ig);
         // C n_e^2 T_e^-1/2 g^2, and nu0 / T_e per unit observed frequency
         const float Q = m.pref0 * __expf(m.lr_pref * lr + m.c2_pref * c * c) * gg * gg;
         const float xi = ig * m.inv_T0 * __expf(m.T_index * lr);
@@ -879,11 +916,12 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
                                      o.status == ODX_DISK_HIT);
     store_record(A.records + id, r);
     if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
-        if (S.s.emitter == ODX_EMIT_TORUS) {
+        if (S.s.emitter == ODX_EMIT_TORUS || S.s.emitter == ODX_EMIT_SYNCH) {
+            const double Ij = S.s.emitter == ODX_EMIT_SYNCH ? synch_constants(S.s).Aj : 1.0;
             for (int k = 0; k < S.s.n_freq; ++k) {
                 const float2 p = *reinterpret_cast<const float2 *>(img + (int64_t)k * S.n_rays);
                 const double nu = S.s.freqs[k];
-                img[(int64_t)k * S.n_rays] = nu * nu * nu * df_get(p.x, p.y);
+                img[(int64_t)k * S.n_rays] = nu * nu * nu * Ij * df_get(p.x, p.y);
             }
         } else {
             img[0] = r.intensity;

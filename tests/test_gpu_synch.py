@@ -1,0 +1,104 @@
+"""Keplerian synchrotron shell (Section 4.5) on the GPU against the oracle, through the C ABI:
+FP64 path pixel by pixel, mixed path by image error and sampled pixels of a full-size image,
+image-integrated spectra.  The oracle evaluates the coefficients in CGS with its own K_2
+(Gauss-Legendre); the CUDA path in scaled units with a trapezoidal K_2."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_02063_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_INTENSITY, STATUS_AGREE, IMG_ERR = 1e-8, 0.999, 1e-3
+
+
+@pytest.fixture(scope="module")
+def tracer():
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    from paper_1601_02063_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    tr = B.Tracer(0)
+    yield tr
+    tr.close()
+
+
+def _render(tracer, scenes):
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    rec, img = tracer.render(scenes)
+    torch.cuda.synchronize()
+    return B.records_to_numpy(rec)[:B.n_rays(scenes)], img[:B.n_image(scenes)].cpu().numpy()
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.998])
+def test_fp64_shell_matches_oracle(tracer, orc, a):
+    """40 x 36 pixels (ragged tiles) over +-15 M at 150, 340, 1000 GHz."""
+    sc = W.synch_shell(a=a, precision="fp64")
+    sc.update(n_alpha=40, n_beta=36)
+    got, img = _render(tracer, sc)
+    ref = orc.render(sc)
+    same = got["status"] == ref["status"]
+    assert np.mean(same) >= STATUS_AGREE
+    n = 40 * 36
+    for k in range(3):
+        I_ref, I_got = ref["I_nu"][:, k], img[k * n:(k + 1) * n]
+        rel = _rel(I_got[same], I_ref[same])
+        assert np.mean(rel <= REL_INTENSITY) >= STATUS_AGREE and rel.max() <= 1e-6, (k, rel.max())
+        assert I_ref.max() > 0 and np.all(I_got >= 0)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.998])
+def test_mixed_shell_image_error(tracer, orc, a):
+    sc = W.synch_shell(a=a, n=48, precision="mixed")
+    got, img = _render(tracer, sc)
+    ref = orc.render(dict(sc, precision="fp64"))
+    n = 48 * 48
+    for k in range(3):
+        I_ref = ref["I_nu"][:, k]
+        err = np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum()
+        print(f"a={a} nu index {k}: image error {err:.3e}")
+        assert err <= IMG_ERR
+    assert np.mean(got["status"] != ref["status"]) < 0.01
+
+
+def test_mixed_full_size_shell_sampled_pixels(tracer, orc):
+    """The 256 x 256 shell image in the default launch; 300 sampled pixels from the oracle.
+    The transfer terms are not under step control and the FP32 stages step at rtol 1e-6
+    against the oracle's 1e-8, so rays through the hot inner shell differ by the integration
+    error of the steeply varying emissivity: the oracle itself in FP64 at rtol 1e-6 shows
+    the same per-pixel spread (a few per cent of pixels between 1e-3 and 2e-3)."""
+    sc = W.synch_shell(a=0.5, n=256, precision="mixed")
+    got, img = _render(tracer, sc)
+    n = 256 * 256
+    pix = W.sample_pixels(n, 300)
+    ref = orc.render(dict(sc, precision="fp64"), pixels=pix)
+    same = got["status"][pix] == ref["status"]
+    for k in range(3):
+        rel = _rel(img[k * n + pix][same], ref["I_nu"][same, k])
+        assert np.mean(rel <= 1e-3) >= 0.95 and rel.max() <= 1e-2, (k, rel.max())
+
+
+def test_shell_spectrum_matches_oracle(tracer, orc):
+    """Image-integrated F_nu of the FP64 shell image against the oracle's image sums."""
+    import torch
+    from oracle import spectra as S
+    from paper_1601_02063_gb300 import binding as B
+    sc = W.synch_shell(a=0.5, precision="fp64")
+    sc.update(n_alpha=32, n_beta=32)
+    rec, img = tracer.render(sc)
+    flux = torch.zeros(3, dtype=torch.float64, device=img.device)
+    B.odx_image_flux(tracer.ctx, sc, img.data_ptr(), flux.data_ptr())
+    torch.cuda.synchronize()
+    ref = orc.render(sc)
+    F_ref = S.image_flux(sc, S.image_planes(sc, ref))
+    assert np.all(F_ref > 0)
+    assert np.allclose(flux.cpu().numpy(), F_ref, rtol=1e-8, atol=0)
