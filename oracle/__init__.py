@@ -21,7 +21,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 MAX_FREQ = 8
 
 STATUS = {"running": 0, "escaped": 1, "captured": 2, "disk_hit": 3, "maxsteps": 4, "numerr": 5}
-EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4, "synch": 5}
+EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4, "synch": 5, "spot": 6}
 CONVENTIONS = {"physical": 0, "literal": 1}
 
 
@@ -55,6 +55,8 @@ class Scene(C.Structure):
         ("horizon_factor", C.c_double),
         ("max_steps", C.c_int32), ("convention", C.c_int32),
         ("n_e0", C.c_double), ("beta_B", C.c_double), ("mass", C.c_double),
+        ("spot_r", C.c_double), ("spot_size", C.c_double), ("spot_phase", C.c_double),
+        ("t_obs", C.c_double),
     ]
 
 
@@ -96,6 +98,8 @@ def lib():
             "orc_circ_E": (D, [D, D]),
             "orc_circ_L": (D, [D, D]),
             "orc_bessel_k2": (D, [D]),
+            "orc_spot_region": (D, [P(Scene), D, P(D), P(D)]),
+            "orc_spot_omega": (D, [P(Scene)]),
             "orc_r_g": (D, [D]),
             "orc_synch_coeffs": (None, [P(Scene), D, D, D, P(D), P(D)]),
             "orc_ck_tableau": (None, [P(D), P(D), P(D), P(D)]),
@@ -143,6 +147,8 @@ def make_scene(d: dict) -> Scene:
     sc.n_e0 = float(d.get("n_e0", 0.0))
     sc.beta_B = float(d.get("beta_B", 0.0))
     sc.mass = float(d.get("mass", 0.0))
+    for k in ("spot_r", "spot_size", "spot_phase", "t_obs"):
+        setattr(sc, k, float(d.get(k, 0.0)))
     cn = d.get("C_norm")
     if cn is None:
         cn = torus_norm(d["a"], d.get("nu_norm", 1.0), d["ne_index"], d["T0"], d["T_index"],
@@ -245,6 +251,19 @@ def nt_flux(a: float, r: float) -> float:
 def bessel_k2(x: float) -> float:
     """K_2(x) by quadrature of its integral definition."""
     return lib().orc_bessel_k2(float(x))
+
+
+def spot_omega(scene: dict) -> float:
+    """Angular velocity of the hot spot's circular orbit."""
+    return lib().orc_spot_omega(C.byref(make_scene(scene)))
+
+
+def spot_region(scene: dict, y, sgn: float = -1.0) -> tuple[float, float]:
+    """(max(d - 4 r_spot, -z), d) of the hot spot at state y (r, theta, phi, t, ...)."""
+    yy = (C.c_double * 6)(*[float(v) for v in list(y)[:6]])
+    d = C.c_double()
+    v = lib().orc_spot_region(C.byref(make_scene(scene)), float(sgn), yy, C.byref(d))
+    return v, d.value
 
 
 def r_g(mass: float) -> float:

@@ -38,6 +38,7 @@
 #define ORC_EMIT_CONST 3     /* test medium: dtau/ds = kappa, dI/ds = eps e^-tau */
 #define ORC_EMIT_NT_DISK 4   /* Novikov-Thorne disk: blackbody at T0 (8 pi F / 3)^1/4 */
 #define ORC_EMIT_SYNCH 5     /* Keplerian shell, thermal synchrotron (Section 4.5, CGS) */
+#define ORC_EMIT_SPOT 6      /* optically thick Keplerian hot spot (Section 4.4)       */
 
 /* sign conventions for the traced photon (see the direction reading in the design notes) */
 #define ORC_CONV_PHYSICAL 0 /* real outgoing photon, traced back in affine time */
@@ -62,6 +63,10 @@ typedef struct {
      * Theta_e = T0 r^-T_index, B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r) [G], black-hole mass
      * [solar masses] (lengths in r_g = G M / c^2), freqs in Hz, emission for r <= r_out */
     double n_e0, beta_B, mass;
+    /* hot spot: centre on the equatorial circular orbit of radius spot_r (<= 0: r_ISCO),
+     * azimuth spot_phase + Omega t; Gaussian width spot_size (r_spot); the image is the one
+     * seen at observer time t_obs; emitted I_nu = C_norm exp(-d^2 / (2 r_spot^2)) B_nu(T0) */
+    double spot_r, spot_size, spot_phase, t_obs;
 } orc_scene;
 
 typedef struct {
@@ -99,6 +104,10 @@ double orc_bessel_k2(double x);
 double orc_r_g(double mass);
 void orc_synch_coeffs(const orc_scene *sc, double r, double cost, double nu0, double *j,
                       double *alpha);
+/* Hot spot (Section 4.4): the region function max(d - 4 r_spot, -z) at state y (t = y[3])
+ * for the traced direction sign sgn, and the spot centre's orbital angular velocity. */
+double orc_spot_region(const orc_scene *sc, double sgn, const double y[6], double *d);
+double orc_spot_omega(const orc_scene *sc);
 double orc_torus_norm(double a, double nu, double ne_index, double T0, double T_index,
                       double r_outer);
 int orc_trace_ray(const orc_scene *sc, double alpha, double beta, orc_result *out);

@@ -27,14 +27,14 @@ def pixel_solid_angle(scene: dict) -> float:
 
 
 def planes_of(scene: dict) -> int:
-    return len(scene["freqs"]) if scene["emitter"] in ("torus", "nt_disk", "synch") else 1
+    return len(scene["freqs"]) if scene["emitter"] in ("torus", "nt_disk", "synch", "spot") else 1
 
 
 def image_planes(scene: dict, results: np.ndarray) -> np.ndarray:
     """[planes][n_beta * n_alpha] image from oracle results in pixel order: I_nu per
     frequency for the torus, the Novikov-Thorne disk and the synchrotron shell, the thin-disk
     intensity otherwise."""
-    if scene["emitter"] in ("torus", "nt_disk", "synch"):
+    if scene["emitter"] in ("torus", "nt_disk", "synch", "spot"):
         return np.ascontiguousarray(results["I_nu"][:, :planes_of(scene)].T)
     return np.ascontiguousarray(results["intensity"][None, :])
 

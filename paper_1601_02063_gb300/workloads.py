@@ -31,6 +31,9 @@ _DEFAULTS = dict(
     rtol_fp32=1e-6, r_switch=0.0,
     # synchrotron shell: n_e at r = 1 [cm^-3], field parameter beta_B, mass [M_sun]
     n_e0=3e7, beta_B=10.0, mass=4e6,
+    # hot spot: orbit radius (<= 0: r_ISCO), Gaussian width r_spot, phase at t = 0, the
+    # observer time of the image
+    spot_r=0.0, spot_size=0.5, spot_phase=0.0, t_obs=0.0,
 )
 
 
@@ -104,6 +107,19 @@ def synch_shell(a: float = 0.0, n: int = 256, precision: str = "mixed",
                  freqs=list(freqs), r_out=500.0, ne_index=1.1, theta_width=10.0, T0=100.0,
                  T_index=0.84, n_e0=3e7, beta_B=10.0, mass=4e6, hmax_frac=0.05,
                  precision=precision)
+
+
+def hot_spot(t_obs: float = 0.0, a: float = 0.0, n: int = 128, precision: str = "fp64") -> dict:
+    """Optically thick Keplerian hot spot (Section 4.4): centre on the circular equatorial
+    orbit at r_ISCO, r_spot = 0.5 M (the spot is the region d < 4 r_spot, z > 0), seen at
+    i = 60 deg over [-10, 10]^2 M at observer time t_obs; blackbody at T0 = 1 times the
+    Gaussian profile, 8 frequencies log-spaced in [0.1, 10].  Steps are capped at 0.02 r so
+    that no step crosses the spot without landing inside it (chords below ~0.1 M)."""
+    freqs = [float(v) for v in np.geomspace(0.1, 10.0, 8)]
+    return scene(a=a, theta_obs=math.radians(60.0), alpha_min=-10.0, alpha_max=10.0,
+                 beta_min=-10.0, beta_max=10.0, n_alpha=n, n_beta=n, emitter="spot",
+                 freqs=freqs, T0=1.0, C_norm=1.0, spot_r=0.0, spot_size=0.5,
+                 spot_phase=0.0, t_obs=t_obs, hmax_frac=0.02, precision=precision)
 
 
 def sweep_64(seed: int = SEED, precision: str = "mixed") -> list[dict]:

@@ -1,0 +1,75 @@
+"""Pins of the Keplerian hot spot in the oracle (Section 4.4): the coordinate time carried
+along a ray (a radial Schwarzschild ray against t(r) = r + 2 ln(r/2 - 1)); every hit sits
+on the spot's boundary at the emission time t_obs - dt (the spot's orbit typed here from
+Kepler's law); the image repeats after one orbital period; the spectrum of every hit pixel
+is a single Planck law at g T0."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_02063_gb300 import workloads as W
+
+
+def test_coordinate_time_along_radial_schwarzschild_ray(orc):
+    """Equatorial observer, central pixel: L = Q = 0, a radial ray; the traced t (negative:
+    the photon's past) is -dt with dt = (r_obs - r) + 2 ln((r_obs - 2) / (r - 2))."""
+    sc = W.scene(a=0.0, theta_obs=math.pi / 2, emitter="none", n_alpha=1, n_beta=1,
+                 alpha_min=-1e-9, alpha_max=1e-9, beta_min=-1e-9, beta_max=1e-9, rtol=1e-11)
+    s, y, _ = orc.trace_path(sc, 0.0, 0.0)
+    r, t = y[:, 0], y[:, 3]
+    r0 = r[0]
+    keep = r > 2.5
+    dt = (r0 - r[keep]) + 2.0 * np.log((r0 - 2.0) / (r[keep] - 2.0))
+    assert keep.sum() > 20
+    assert np.all(np.abs(-t[keep] - dt) <= 1e-10 * np.maximum(dt, 1.0))
+
+
+def _spot_hits(orc, sc):
+    res = orc.render(sc)
+    return res, np.nonzero(res["status"] == 3)[0]
+
+
+@pytest.mark.parametrize("a,t_obs", [(0.0, 0.0), (0.0, 37.0), (0.9, 11.0)])
+def test_hits_lie_on_spot_boundary_at_emission_time(orc, a, t_obs):
+    sc = W.hot_spot(t_obs=t_obs, a=a, n=40)
+    res, hits = _spot_hits(orc, sc)
+    assert hits.size > 5
+    r_s = orc.isco(a)
+    omega = 1.0 / (r_s ** 1.5 + a)
+    for i in hits:
+        r, th, ph, t = res["y_end"][i, :4]
+        t_e = t_obs + t  # physical tracing: t = -dt
+        phs = sc["spot_phase"] + omega * t_e
+        R, Rs = math.hypot(r, a), math.hypot(r_s, a)
+        d = math.sqrt((R * math.cos(ph) - Rs * math.cos(phs)) ** 2 +
+                      (R * math.sin(ph) - Rs * math.sin(phs)) ** 2 + (r * math.cos(th)) ** 2)
+        z = r * math.cos(th)
+        edge = max(d - 4.0 * sc["spot_size"], -z)
+        assert abs(edge) <= 1e-9, (i, d, z)
+        assert z >= -1e-9 and d <= 4.0 * sc["spot_size"] + 1e-9
+
+
+def test_image_repeats_after_one_orbit(orc):
+    sc = W.hot_spot(t_obs=5.0, n=40)
+    period = 2.0 * math.pi / orc.spot_omega(sc)
+    a, _ = _spot_hits(orc, sc)
+    b, _ = _spot_hits(orc, dict(sc, t_obs=5.0 + period))
+    assert np.sum(a["status"] != b["status"]) <= 1
+    same = (a["status"] == 3) & (b["status"] == 3)
+    assert same.sum() > 5
+    assert np.allclose(a["I_nu"][same], b["I_nu"][same], rtol=1e-8, atol=0)
+
+
+def test_hit_spectra_are_planck_at_g_T0(orc):
+    """I_nu = w B_nu(g T0) with one weight w per pixel: the ratios across frequencies are
+    those of a Planck law at the pixel's g T0 (B_nu = 2 nu^3 / (e^(nu/T) - 1))."""
+    sc = W.hot_spot(t_obs=20.0, n=40)
+    res, hits = _spot_hits(orc, sc)
+    nu = np.asarray(sc["freqs"])
+    for i in hits:
+        gT = res["g"][i] * sc["T0"]
+        B = 2.0 * nu ** 3 / np.expm1(nu / gT)
+        w = res["I_nu"][i, :len(nu)] / B
+        assert np.allclose(w, w[0], rtol=1e-12)
+        assert 0.0 < w[0] <= sc["C_norm"]
