@@ -66,6 +66,17 @@ extern "C" {
                                 r_g = G mass / c^2; the flow is the torus's.  The printed
                                 emissivity integrates over directions: the transfer uses
                                 j_nu / 4 pi per steradian */
+#define ODX_EMIT_SPOT 5      /* optically thick Keplerian hot spot (Section 4.4), FP64 path
+                                only: the centre orbits the equatorial circle r = spot_r
+                                (<= 0: r_ISCO) at Omega = 1/(r^1.5 + a), azimuth spot_phase +
+                                Omega t; a photon seen at t_obs left its point at t_obs - dt
+                                (dt: coordinate time along the ray); the spot is d < 4
+                                spot_size, z > 0 in the pseudo-Cartesian coordinates x, y =
+                                sqrt(r^2 + a^2) (cos, sin) phi, z = r cos theta; a ray ends
+                                at its first entry (status ODX_DISK_HIT) and sees
+                                C_norm exp(-d^2 / (2 spot_size^2)) B_nu(g T0) at the n_freq
+                                frequencies (n_freq image planes; record intensity: the
+                                bolometric value), g for gas co-rotating at Omega */
 
 /* arithmetic of the integrator */
 #define ODX_FP64 0  /* every stage in FP64                                             */
@@ -107,6 +118,10 @@ typedef struct odx_scene {
     double n_e0;                    /* synchrotron shell: n_e at r = 1 (cm^-3), > 0      */
     double beta_B;                  /* synchrotron shell: field parameter, > 0           */
     double mass;                    /* synchrotron shell: black-hole mass (M_sun), > 0   */
+    double spot_r;                  /* hot spot: orbit radius (<= 0: r_ISCO)             */
+    double spot_size;               /* hot spot: Gaussian width r_spot (> 0)             */
+    double spot_phase;              /* hot spot: azimuth of the centre at t = 0          */
+    double t_obs;                   /* hot spot: observer time of the image              */
 } odx_scene;
 
 /*
@@ -352,7 +367,7 @@ int32_t odx_surrogate_render(odx_mlp *mlp, const odx_scene *scene_host, double b
  * is a deployment variant of odx_render.
  *
  * The ray queue counter, the device statistics and the scene table live in one file-scope
- * device array of 32,768 bytes that every GPU loading this library holds until the process
+ * device array of 36,864 bytes that every GPU loading this library holds until the process
  * exits; at most ODX_STATIC_MAX_SCENES scenes per call (more: ODX_ERR_TOO_LARGE, nothing
  * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
  * as odx_render) and the scene descriptions in host memory.  The call works on the calling

@@ -684,6 +684,15 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
             break;
         }
         if (h > sc->hmax_frac * y[0]) h = sc->hmax_frac * y[0];
+        if (sc->emitter == ORC_EMIT_SPOT) {
+            /* reading: no step may carry a ray across the spot unseen, |h| <= (d - 4 r_spot)
+             * / 2 (a photon moves at most ~1 in these coordinates per unit affine parameter
+             * away from the hole), but not below r_spot / 4 */
+            double d;
+            orc_spot_region(sc, rc.sgn, y, &d);
+            double cap = fmax(0.5 * (d - 4.0 * sc->spot_size), 0.25 * sc->spot_size);
+            if (h > cap) h = cap;
+        }
         derivs(&rc, rc.n, y, k1);
         for (int i = 0; i < N_GEO; ++i) yscal[i] = fabs(y[i]) + fabs(h * k1[i]) + 1e-30;
 

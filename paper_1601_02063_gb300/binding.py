@@ -20,7 +20,7 @@ MAX_FREQ = 8
  ERR_TOO_LARGE) = range(8)
 STATIC_MAX_SCENES = 64
 RUNNING, ESCAPED, CAPTURED, DISK_HIT, MAXSTEPS, NUMERR = range(6)
-EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "nt_disk": 3, "synch": 4}
+EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "nt_disk": 3, "synch": 4, "spot": 5}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 CONVENTIONS = {"physical": 0, "literal": 1}
 
@@ -43,6 +43,8 @@ class odx_scene(C.Structure):
         ("precision", C.c_int32), ("reserved", C.c_int32),
         ("rtol_fp32", C.c_double), ("r_switch", C.c_double),
         ("n_e0", C.c_double), ("beta_B", C.c_double), ("mass", C.c_double),
+        ("spot_r", C.c_double), ("spot_size", C.c_double), ("spot_phase", C.c_double),
+        ("t_obs", C.c_double),
     ]
 
 
@@ -77,7 +79,7 @@ RECORD_DTYPE = np.dtype([
 ])
 RECORD_BYTES = 80
 assert C.sizeof(odx_ray_record) == RECORD_BYTES == RECORD_DTYPE.itemsize
-assert C.sizeof(odx_scene) == 296
+assert C.sizeof(odx_scene) == 328
 
 # (name, restype, argtypes) of every entry point in include/odyssey.h
 _P = C.c_void_p
@@ -350,7 +352,7 @@ def scene_struct(d: dict) -> odx_scene:
     for k in ("a", "r_obs", "theta_obs", "phi_obs", "alpha_min", "alpha_max", "beta_min",
               "beta_max", "r_in", "r_out", "q_emis", "ne_index", "theta_width", "T0",
               "T_index", "rtol", "h0", "hmax_frac", "horizon_factor", "rtol_fp32", "r_switch",
-              "n_e0", "beta_B", "mass"):
+              "n_e0", "beta_B", "mass", "spot_r", "spot_size", "spot_phase", "t_obs"):
         setattr(s, k, float(d[k]))
     s.n_alpha, s.n_beta = int(d["n_alpha"]), int(d["n_beta"])
     s.emitter = EMITTERS[d["emitter"]]
@@ -387,7 +389,7 @@ def n_rays(scenes) -> int:
 
 
 def image_planes(d: dict) -> int:
-    return len(d["freqs"]) if d["emitter"] in ("torus", "nt_disk", "synch") else 1
+    return len(d["freqs"]) if d["emitter"] in ("torus", "nt_disk", "synch", "spot") else 1
 
 
 def n_image(scenes) -> int:

@@ -89,7 +89,7 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
         if (s.n_alpha < 1 || s.n_beta < 1)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: resolution must be >= 1", k);
     }
-    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_SYNCH)
+    if (s.emitter < ODX_EMIT_NONE || s.emitter > ODX_EMIT_SPOT)
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown emitter %d", k, s.emitter);
     if (odx::disk_emitter(s.emitter) &&
         (!finite(s.r_in) || !finite(s.r_out) || !(s.r_out > 0.0) || !finite(s.q_emis)))
@@ -97,7 +97,7 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
     if (s.emitter == ODX_EMIT_NT_DISK && (!(s.T0 > 0.0) || !finite(s.T0)))
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: NT disk needs T0 > 0", k);
     if (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK ||
-        s.emitter == ODX_EMIT_SYNCH) {
+        s.emitter == ODX_EMIT_SYNCH || s.emitter == ODX_EMIT_SPOT) {
         if (s.n_freq < 1 || s.n_freq > ODX_MAX_FREQ)
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: n_freq must be 1..%d", k, ODX_MAX_FREQ);
         for (int f = 0; f < s.n_freq; ++f)
@@ -115,6 +115,14 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
             !(s.theta_width > 0.0) || !finite(s.theta_width) || !finite(s.ne_index) ||
             !finite(s.T_index) || !finite(s.r_out) || !(s.r_out > 0.0))
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad synchrotron-shell parameters", k);
+    }
+    if (s.emitter == ODX_EMIT_SPOT) {
+        if (!(s.spot_size > 0.0) || !finite(s.spot_size) || !finite(s.spot_r) ||
+            !finite(s.spot_phase) || !finite(s.t_obs) || !(s.T0 > 0.0) || !finite(s.T0) ||
+            !(s.C_norm >= 0.0) || !finite(s.C_norm))
+            return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad hot-spot parameters", k);
+        if (s.precision != ODX_FP64)
+            return fail(ctx, ODX_ERR_UNSUPPORTED, "scene %d: the hot spot runs on the FP64 path", k);
     }
     if (!(s.rtol > 0.0) || !finite(s.rtol) || !(s.h0 > 0.0) || !finite(s.h0) ||
         !(s.hmax_frac > 0.0) || !finite(s.hmax_frac) || !(s.horizon_factor > 1.0) ||

@@ -9,12 +9,12 @@
 
 namespace odx {
 
-// Image planes of a scene: one per observed frequency for the torus, the Novikov-Thorne disk
-// and the synchrotron shell, otherwise one (thin-disk intensity, or zero for geodesics only).
+// Image planes of a scene: one per observed frequency for the torus, the Novikov-Thorne disk,
+// the synchrotron shell and the hot spot, otherwise one (thin-disk intensity, or zero for geodesics only).
 __host__ __device__ inline int32_t scene_planes(const odx_scene &s)
 {
     return (s.emitter == ODX_EMIT_TORUS || s.emitter == ODX_EMIT_NT_DISK ||
-            s.emitter == ODX_EMIT_SYNCH)
+            s.emitter == ODX_EMIT_SYNCH || s.emitter == ODX_EMIT_SPOT)
                ? s.n_freq
                : 1;
 }

@@ -30,7 +30,7 @@ using odx::DevStats;
 constexpr size_t kQueueOffset = 0;
 constexpr size_t kStatsOffset = 64;
 constexpr size_t kScenesOffset = 256;
-constexpr size_t kStaticBytes = 32768;
+constexpr size_t kStaticBytes = 36864;
 static_assert(kScenesOffset + ODX_STATIC_MAX_SCENES * sizeof(DevScene) <= kStaticBytes,
               "scene table does not fit the static scratch");
 static_assert(sizeof(DevStats) <= kScenesOffset - kStatsOffset, "stats do not fit");

@@ -126,6 +126,73 @@ __device__ inline double nt_disk_planes(const DevScene &S, double *img, double a
     return hit ? 12.987878804533656 * gT * gT * gT * gT : 0.0;  // 2 pi^4 / 15
 }
 
+// ---- Keplerian hot spot (Section 4.4) -------------------------------------------------------
+__host__ __device__ inline double spot_orbit_radius(const odx_scene &s)
+{
+    return s.spot_r > 0.0 ? s.spot_r : isco_radius(s.a);
+}
+__host__ __device__ inline double spot_omega(const odx_scene &s)
+{
+    const double rs = spot_orbit_radius(s);
+    return 1.0 / (rs * sqrt(rs) + s.a);
+}
+
+// max(d - 4 r_spot, -z) at state y (negative inside the spot) and d.  The photon at y reaches
+// the image plane dt = sgn t later in coordinate time (t runs from 0 there with dt/ds =
+// sgn dt/dlambda), so it left y at t_e = t_obs - sgn t, when the spot centre was at azimuth
+// spot_phase + Omega t_e on the circle r = spot_r.  Distances in the pseudo-Cartesian
+// coordinates x, y = sqrt(r^2 + a^2) (cos phi, sin phi), z = r cos theta.
+__device__ inline double spot_region(const odx_scene &s, double sgn, const double y[6], double &d)
+{
+    const double rs = spot_orbit_radius(s);
+    const double phs = s.spot_phase + spot_omega(s) * (s.t_obs - sgn * y[3]);
+    const double Rs = sqrt(rs * rs + s.a * s.a), R = sqrt(y[0] * y[0] + s.a * s.a);
+    double sp, cp, ss, cs, st, ct;
+    sincos(y[2], &sp, &cp);
+    sincos(phs, &ss, &cs);
+    sincos(y[1], &st, &ct);
+    const double dx = R * cp - Rs * cs, dy = R * sp - Rs * ss, z = y[0] * ct;
+    d = sqrt(dx * dx + dy * dy + z * z);
+    return fmax(d - 4.0 * s.spot_size, -z);
+}
+
+// Step cap near the spot: no step may carry a ray across it unseen, |h| <= (d - 4 r_spot) / 2,
+// but not below r_spot / 4.
+__device__ inline double spot_step_cap(const odx_scene &s, double sgn, const double y[6])
+{
+    double d;
+    spot_region(s, sgn, y, d);
+    return fmax(0.5 * (d - 4.0 * s.spot_size), 0.25 * s.spot_size);
+}
+
+// Redshift of gas co-rotating with the spot centre at Omega at (r, theta): g = 1 / (u^t
+// (1 - Omega L)) (Eq. 2), u^t from u.u = -1; zero where that motion is not timelike.
+__device__ inline double spot_redshift(const odx_scene &s, double r, double theta, double L)
+{
+    const double a = s.a;
+    double st, ct;
+    sincos(theta, &st, &ct);
+    st = fmax(st, kSinFloor);
+    const double Sig = r * r + a * a * ct * ct, Del = r * r - 2.0 * r + a * a;
+    const double A = (r * r + a * a) * (r * r + a * a) - a * a * Del * st * st;
+    const double Om = spot_omega(s);
+    const double N = -(1.0 - 2.0 * r / Sig) - 2.0 * (2.0 * a * r * st * st / Sig) * Om +
+                     A * st * st / Sig * Om * Om;
+    return N < 0.0 ? sqrt(-N) / (1.0 - Om * L) : 0.0;
+}
+
+// Image planes of a spot hit: w B_nu(g T0) with w = C_norm exp(-d^2 / (2 r_spot^2)) at the
+// entry point (I_nu / nu^3 invariant); zero for rays that miss.  Returns the bolometric
+// intensity w (2 pi^4 / 15) (g T0)^4.
+__device__ inline double spot_planes(const DevScene &S, double *img, double w, double g, bool hit)
+{
+    const double gT = hit ? g * S.s.T0 : 0.0;
+    if (img)
+        for (int k = 0; k < S.s.n_freq; ++k)
+            img[(int64_t)k * S.n_rays] = hit ? w * planck(S.s.freqs[k], gT) : 0.0;
+    return hit ? w * 12.987878804533656 * gT * gT * gT * gT : 0.0;  // 2 pi^4 / 15
+}
+
 struct RecordOut {
     int32_t status, n_acc, n_rej, n_cross;
     double r_cross, phi_cross, r_hit, phi_hit, g, intensity, H_end, Q_drift;

@@ -77,6 +77,29 @@ __device__ __noinline__ void locate_crossing64(const Geo<double> &g, const doubl
     for (int i = 0; i < 6; ++i) yc[i] = y5[i];
 }
 
+// First entry into the hot spot inside an accepted step: bisection on the size of a single
+// fifth-order step from the step start (60 halvings), ending inside; returns the state.
+__device__ __noinline__ void locate_spot64(const Geo<double> &g, const odx_scene &s,
+                                           const double y[6], const double k1[6], double h,
+                                           double yc[6])
+{
+    double lo = 0.0, hi = h, dy[6], yt[6], d;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        ck_geo_increment<double>(g, y, k1, mid, dy);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) yt[i] = y[i] + dy[i];
+        if (spot_region(s, g.sgn, yt, d) < 0.0)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    ck_geo_increment<double>(g, y, k1, hi, dy);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
+}
+
+// For the hot spot, inten carries the Gaussian weight w of the entry point.
 template <int NF>
 __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScene &S,
                                                const Ray64<NF> &R, int32_t status,
@@ -100,8 +123,10 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     if (S.s.emitter == ODX_EMIT_NT_DISK)
         o.intensity = nt_disk_planes(S, img, R.a, ray_r_isco(A, S, R.a), r_hit, g,
                                      status == ODX_DISK_HIT);
+    if (S.s.emitter == ODX_EMIT_SPOT)
+        o.intensity = spot_planes(S, img, inten, g, status == ODX_DISK_HIT);
     store_record(A.records + R.id, o);
-    if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
+    if (img && S.s.emitter != ODX_EMIT_NT_DISK && S.s.emitter != ODX_EMIT_SPOT) {
         if constexpr (NF > 0) {
             // synchrotron shell: the stages carry I_nu / (nu^3 Aj), nu in Hz
             const double Ij = S.s.emitter == ODX_EMIT_SYNCH ? synch_constants(S.s).Aj : 1.0;
@@ -163,6 +188,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             const Geo<double> g{R.a, R.L, R.sgn};
             derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
             R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);
+            if (S.s.emitter == ODX_EMIT_SPOT) R.h = fmin(R.h, spot_step_cap(S.s, R.sgn, R.y));
             R.hs = R.h;
             live = true;
         }
@@ -211,6 +237,18 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         status = ODX_DISK_HIT;
                     }
                 }
+                double d_spot;
+                if (status == ODX_RUNNING && S.s.emitter == ODX_EMIT_SPOT &&
+                    spot_region(S.s, R.sgn, y5, d_spot) < 0.0) {  // first entry into the spot
+                    double yc[6];
+                    locate_spot64(g, S.s, R.y, R.k1, h, yc);
+                    spot_region(S.s, R.sgn, yc, d_spot);
+                    const double w = S.s.C_norm * exp(-d_spot * d_spot /
+                                                      (2.0 * S.s.spot_size * S.s.spot_size));
+                    write_result64<NF>(A, S, R, ODX_DISK_HIT, yc, yc[0], yc[2],
+                                       spot_redshift(S.s, yc[0], yc[1], R.L), w);
+                    status = ODX_DISK_HIT;
+                }
                 if (status == ODX_RUNNING) {
 #pragma unroll
                     for (int i = 0; i < 6; ++i) R.y[i] = y5[i];
@@ -226,6 +264,8 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         if (R.k1[0] > 0.0 && R.y[0] > R.r_start) status = ODX_ESCAPED;
                     }
                     R.h = fmin(h_next, S.s.hmax_frac * R.y[0]);
+                    if (S.s.emitter == ODX_EMIT_SPOT)
+                        R.h = fmin(R.h, spot_step_cap(S.s, R.sgn, R.y));
                     R.hs = R.h;
                 }
             } else {

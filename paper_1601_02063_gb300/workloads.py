@@ -113,13 +113,12 @@ def hot_spot(t_obs: float = 0.0, a: float = 0.0, n: int = 128, precision: str = 
     """Optically thick Keplerian hot spot (Section 4.4): centre on the circular equatorial
     orbit at r_ISCO, r_spot = 0.5 M (the spot is the region d < 4 r_spot, z > 0), seen at
     i = 60 deg over [-10, 10]^2 M at observer time t_obs; blackbody at T0 = 1 times the
-    Gaussian profile, 8 frequencies log-spaced in [0.1, 10].  Steps are capped at 0.02 r so
-    that no step crosses the spot without landing inside it (chords below ~0.1 M)."""
+    Gaussian profile, 8 frequencies log-spaced in [0.1, 10]."""
     freqs = [float(v) for v in np.geomspace(0.1, 10.0, 8)]
     return scene(a=a, theta_obs=math.radians(60.0), alpha_min=-10.0, alpha_max=10.0,
                  beta_min=-10.0, beta_max=10.0, n_alpha=n, n_beta=n, emitter="spot",
                  freqs=freqs, T0=1.0, C_norm=1.0, spot_r=0.0, spot_size=0.5,
-                 spot_phase=0.0, t_obs=t_obs, hmax_frac=0.02, precision=precision)
+                 spot_phase=0.0, t_obs=t_obs, precision=precision)
 
 
 def sweep_64(seed: int = SEED, precision: str = "mixed") -> list[dict]:

@@ -1,0 +1,98 @@
+"""Keplerian hot spot (Section 4.4) on the FP64 CUDA path against the oracle, through the C
+ABI: hit statuses, entry points, redshifts and the blackbody planes per pixel; a light curve
+and spectrogram over one orbit as one batched launch, reduced by odx_image_flux, against the
+oracle's image sums; the image repeats after one orbital period; the mixed path refuses
+the emitter."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_02063_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tracer():
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    from paper_1601_02063_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+    tr = B.Tracer(0)
+    yield tr
+    tr.close()
+
+
+def _render(tracer, scenes):
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    rec, img = tracer.render(scenes)
+    torch.cuda.synchronize()
+    return B.records_to_numpy(rec)[:B.n_rays(scenes)], img[:B.n_image(scenes)].cpu().numpy()
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+@pytest.mark.parametrize("a,t_obs", [(0.0, 0.0), (0.0, 37.0), (0.9, 11.0)])
+def test_spot_image_matches_oracle(tracer, orc, a, t_obs):
+    sc = W.hot_spot(t_obs=t_obs, a=a, n=56)
+    sc.update(n_beta=50)
+    got, img = _render(tracer, sc)
+    ref = orc.render(sc)
+    same = got["status"] == ref["status"]
+    assert np.mean(same) >= 0.999
+    hit = same & (ref["status"] == 3)
+    assert hit.sum() > 10
+    for f in ("r_hit", "phi_hit", "g"):
+        assert _rel(got[f][hit], ref[f][hit]).max() <= 1e-9, f
+    n = 56 * 50
+    for k in range(len(sc["freqs"])):
+        I_got, I_ref = img[k * n:(k + 1) * n], ref["I_nu"][:, k]
+        assert _rel(I_got[hit], I_ref[hit]).max() <= 1e-8, k
+        assert np.all(I_got[~(got["status"] == 3)] == 0.0)
+
+
+def test_spot_light_curve_over_one_orbit(tracer, orc):
+    """16 observer times over one orbital period in one launch; F_nu per image against the
+    oracle's sums of its own images."""
+    import torch
+    from oracle import spectra as S
+    from paper_1601_02063_gb300 import binding as B
+    base = W.hot_spot(n=32)
+    period = 2.0 * math.pi / orc.spot_omega(base)
+    scenes = [dict(base, t_obs=period * j / 16.0) for j in range(16)]
+    rec, img = tracer.render(scenes)
+    nf = len(base["freqs"])
+    flux = torch.zeros(16 * nf, dtype=torch.float64, device=img.device)
+    lum = torch.zeros(16, dtype=torch.float64, device=img.device)
+    B.odx_image_flux(tracer.ctx, scenes, img.data_ptr(), flux.data_ptr(), lum.data_ptr())
+    torch.cuda.synchronize()
+    flux = flux.cpu().numpy().reshape(16, nf)
+    for j in (0, 5, 11):
+        ref = orc.render(scenes[j])
+        F_ref = S.image_flux(scenes[j], S.image_planes(scenes[j], ref))
+        assert np.allclose(flux[j], F_ref, rtol=1e-8, atol=0), j
+        assert math.isclose(float(lum[j]), S.light_curve_point(scenes[j], F_ref), rel_tol=1e-8)
+    assert flux.max() > 0 and lum.cpu().numpy().std() > 0  # the spot's flux varies with phase
+
+
+def test_spot_image_repeats_after_one_period(tracer, orc):
+    base = W.hot_spot(t_obs=3.0, n=48)
+    period = 2.0 * math.pi / orc.spot_omega(base)
+    g1, i1 = _render(tracer, base)
+    g2, i2 = _render(tracer, dict(base, t_obs=3.0 + period))
+    assert np.sum(g1["status"] != g2["status"]) <= 1
+    both = (g1["status"] == 3) & (g2["status"] == 3)
+    n = 48 * 48
+    assert np.allclose(i1[:n][both], i2[:n][both], rtol=1e-8, atol=0)
+
+
+def test_spot_mixed_precision_is_refused(tracer):
+    from paper_1601_02063_gb300 import binding as B
+    with pytest.raises(B.OdxError):
+        tracer.render(W.hot_spot(n=8, precision="mixed"))
