@@ -426,7 +426,7 @@ def run_ours(args):
     # inclinations (5..80 deg), 256^2 each, rendered in one batched launch and reduced to
     # F_nu per image and its integral over nu; and the reduction alone on the 512^2 image
     spectra = None
-    if args.precision == "mixed" and args.size == 512:
+    if args.precision == "mixed" and args.size == 512 and args.spectra:
         incs = [5.0 + 5.0 * k for k in range(16)]
         lc_scenes = [dict(scene, n_alpha=256, n_beta=256, theta_obs=math.radians(i))
                      for i in incs]
@@ -548,7 +548,7 @@ def run_ours(args):
     # a = 0.95, i = 60 deg, FP64) through the FP64 and the mixed path, same metric as the
     # paper's runtime / total steps
     paper_wl = None
-    if args.size == 512:
+    if args.size == 512 and args.spectra:
         from paper_1601_02063_gb300 import workloads as W
         out_p = {}
         for prec in ("fp64", "mixed"):
@@ -694,6 +694,8 @@ def main():
                     help="omit training and timing the learned surrogate")
     ap.add_argument("--no-hard", dest="hard", action="store_false",
                     help="omit the 4096^2 near-edge-on hard case")
+    ap.add_argument("--no-spectra", dest="spectra", action="store_false",
+                    help="omit the spectra, light curves and the paper's timing workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
