@@ -387,7 +387,10 @@ __device__ __forceinline__ void near_horizon(float r, float pr, float a, const P
 // super-Hamiltonian terms F of the FP64 form) and, for NF > 0, the torus transfer terms
 // (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
 // Frequency slots past the scene's n_freq repeat its last frequency (never written out).
-template <int NF, class Med, class Cold>
+// MK, the medium kind of the launch: 0 read per lane from the medium (batched scenes),
+// 1 the torus, 2 the synchrotron shell (single-medium launches: the other emitter's code is
+// not compiled into the stage loop).
+template <int NF, int MK, class Med, class Cold>
 __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, float r_isco,
                                          const float *in, const PairStage &ps, const Cold &C,
                                          float f[6], float *ft, float *fI)
@@ -441,7 +444,8 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, floa
         }
         const float ig = (1.f - Om * L) * rsqrtf(-N);
         const float lr = __logf(r);
-        if (m.synch) {
+        const bool synch = MK == 2 || (MK == 0 && m.synch != 0);
+        if (synch) {
             if (r <= m.r_out) {
                 const float nr = __expf(m.lr_pref * lr + m.c2_pref * c * c);
                 synch32<NF>(m, r, nr, m.inv_T0 * __expf(m.T_index * lr), ig, in + 4, ft, fI);
@@ -507,7 +511,7 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, Cold
 // sum and the error estimate, so no stage derivative is kept; t and phi, which no
 // right-hand side reads, enter only those two sums.  The first stage is evaluated afresh
 // at every attempt (a rejected attempt repeats it exactly).
-template <int NF, class Med>
+template <int NF, int MK, class Med>
 __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<NF> &C,
                                           const Med &mf)
 {
@@ -557,7 +561,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 #pragma unroll 1
     for (int st = 0; st < 6; ++st) {
         float f[6], ft[NF + 1], fI[NF + 1];
-        derivs32<NF>(g, mf, R.r_isco, in, ps, C, f, ft, fI);
+        derivs32<NF, MK>(g, mf, R.r_isco, in, ps, C, f, ft, fI);
         float kf[NG];
         kf[0] = f[0];
         kf[1] = f[1];
@@ -770,7 +774,7 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
 // MINB: resident 128-thread blocks per SM the register allocation is capped for.
 // SINGLE: every ray shares the launch's medium (A.med, read from the kernel parameters, no
 // registers); otherwise each lane keeps its scene's constants.
-template <int NF, int MINB, bool SINGLE>
+template <int NF, int MINB, bool SINGLE, int MK>
 __global__ void __launch_bounds__(kMixedBlock, MINB)
     trace_mixed_kernel(const __grid_constant__ TraceArgs A)
 {
@@ -852,9 +856,9 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
                 R = r64;
             } else {
                 if constexpr (SINGLE)
-                    status = step32<NF>(S, R, C, A.med);
+                    status = step32<NF, MK>(S, R, C, A.med);
                 else
-                    status = step32<NF>(S, R, C, mf);
+                    status = step32<NF, MK>(S, R, C, mf);
             }
             if (status == ODX_RUNNING && C.n_acc[t] + C.n_rej[t] >= S.s.max_steps)
                 status = ODX_MAXSTEPS;
@@ -929,14 +933,14 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     }
 }
 
-template <int NF, bool SINGLE>
+template <int NF, bool SINGLE, int MK>
 cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 grid, cudaStream_t st)
 {
     const dim3 block(L.block);
     switch (L.blocks_per_sm <= 2 ? 2 : (L.blocks_per_sm >= 4 ? 4 : 3)) {
-    case 2: trace_mixed_kernel<NF, 2, SINGLE><<<grid, block, 0, st>>>(args); break;
-    case 3: trace_mixed_kernel<NF, 3, SINGLE><<<grid, block, 0, st>>>(args); break;
-    default: trace_mixed_kernel<NF, 4, SINGLE><<<grid, block, 0, st>>>(args); break;
+    case 2: trace_mixed_kernel<NF, 2, SINGLE, MK><<<grid, block, 0, st>>>(args); break;
+    case 3: trace_mixed_kernel<NF, 3, SINGLE, MK><<<grid, block, 0, st>>>(args); break;
+    default: trace_mixed_kernel<NF, 4, SINGLE, MK><<<grid, block, 0, st>>>(args); break;
     }
     return cudaGetLastError();
 }
@@ -945,10 +949,12 @@ template <int NF>
 cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 grid, cudaStream_t st)
 {
     if constexpr (NF == 0)  // no medium
-        return launch_mixed_nf<NF, true>(args, L, grid, st);
+        return launch_mixed_nf<NF, true, 1>(args, L, grid, st);
+    else if (!args.single_medium)
+        return launch_mixed_nf<NF, false, 0>(args, L, grid, st);
     else
-        return args.single_medium ? launch_mixed_nf<NF, true>(args, L, grid, st)
-                                  : launch_mixed_nf<NF, false>(args, L, grid, st);
+        return args.med.synch ? launch_mixed_nf<NF, true, 2>(args, L, grid, st)
+                              : launch_mixed_nf<NF, true, 1>(args, L, grid, st);
 }
 
 cudaError_t launch_trace_mixed(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
