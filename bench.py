@@ -502,7 +502,7 @@ def run_ours(args):
         # Keplerian hot spot (Section 4.4): 32 observer times over one orbit at r_ISCO
         # (a = 0, i = 60 deg), 64^2 each, FP64 path, one batched launch; the spectrogram
         # F_nu(t_obs) at 8 frequencies and the light curve (its integral over nu)
-        spot0 = W.hot_spot(n=64)
+        spot0 = W.hot_spot(n=64, precision="mixed")
         r_s = 6.0
         period = 2.0 * math.pi * (r_s ** 1.5)
         sp_scenes = [dict(spot0, t_obs=period * j / 32.0) for j in range(32)]
@@ -519,12 +519,19 @@ def run_ours(args):
         st_sp = B.records_to_numpy(rec_sp)[:B.n_rays(sp_scenes)]
         steps_sp = float(st_sp["n_acc"].sum() + st_sp["n_rej"].sum())
         lc = lum_sp.cpu().numpy()
+        sp64 = [dict(sc, precision="fp64") for sc in sp_scenes]
+        tr.render(sp64, out=(rec_sp, img_sp), stream=stream)
+        ms_sp64 = timed(lambda: tr.render(sp64, out=(rec_sp, img_sp), stream=stream), 1)
+        st64 = B.records_to_numpy(rec_sp)[:B.n_rays(sp64)]
+        steps_sp64 = float(st64["n_acc"].sum() + st64["n_rej"].sum())
         spot_info = {"workload": "optically thick Keplerian hot spot at r_ISCO, a = 0, i = 60 deg, "
                                  "r_spot = 0.5 M, 32 observer times over one orbit, 64x64 each "
-                                 "over [-10,10]^2 M, blackbody T0 = 1 at 8 nu in [0.1, 10], FP64, "
-                                 "one launch",
+                                 "over [-10,10]^2 M, blackbody T0 = 1 at 8 nu in [0.1, 10], mixed "
+                                 "precision (FP64 steps within r_spot / 2 of the spot), one launch",
                      "ms_per_light_curve": ms_sp, "rk_steps": steps_sp,
                      "ns_per_photon_step": ms_sp * 1e6 / steps_sp,
+                     "fp64_path": {"ms_per_light_curve": ms_sp64,
+                                   "ns_per_photon_step": ms_sp64 * 1e6 / steps_sp64},
                      "orbital_period_M": period, "nu": spot0["freqs"],
                      "light_curve_normalised": (lc / lc.sum()).tolist(),
                      "spectrogram_F_nu": flux_sp.view(32, 8).tolist()}

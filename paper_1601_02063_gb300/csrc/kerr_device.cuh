@@ -252,4 +252,15 @@ __host__ __device__ inline SynchK synch_constants(const odx_scene &s)
     return k;
 }
 
+// ---- Keplerian hot spot (Section 4.4): the centre's circular equatorial orbit --------------
+__host__ __device__ inline double spot_orbit_radius(const odx_scene &s)
+{
+    return s.spot_r > 0.0 ? s.spot_r : isco_radius(s.a);
+}
+__host__ __device__ inline double spot_omega(const odx_scene &s)
+{
+    const double rs = spot_orbit_radius(s);
+    return 1.0 / (rs * sqrt(rs) + s.a);
+}
+
 }  // namespace odx

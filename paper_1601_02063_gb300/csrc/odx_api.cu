@@ -121,8 +121,6 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
             !finite(s.spot_phase) || !finite(s.t_obs) || !(s.T0 > 0.0) || !finite(s.T0) ||
             !(s.C_norm >= 0.0) || !finite(s.C_norm))
             return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad hot-spot parameters", k);
-        if (s.precision != ODX_FP64)
-            return fail(ctx, ODX_ERR_UNSUPPORTED, "scene %d: the hot spot runs on the FP64 path", k);
     }
     if (!(s.rtol > 0.0) || !finite(s.rtol) || !(s.h0 > 0.0) || !finite(s.h0) ||
         !(s.hmax_frac > 0.0) || !finite(s.hmax_frac) || !(s.horizon_factor > 1.0) ||
@@ -353,6 +351,14 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
         d.f_ky = (float)q.ky;
         d.f_Atau = (float)q.Atau;
     }
+    if (s.emitter == ODX_EMIT_SPOT) {
+        const double rs = spot_orbit_radius(s), om = spot_omega(s);
+        const double two_pi = 6.283185307179586;
+        d.f_spot_Rs = (float)sqrt(rs * rs + s.a * s.a);
+        d.f_spot_om = (float)om;
+        d.f_spot_ph = (float)(s.spot_phase + om * s.t_obs - two_pi * floor((s.spot_phase + om * s.t_obs) / two_pi));
+        d.f_spot_R4 = (float)(4.0 * s.spot_size);
+    }
     const double nu_scale = synch ? 1.0 / kNuUnit : 1.0;
     const int nf = (s.n_freq > 0 && s.n_freq <= ODX_MAX_FREQ) ? s.n_freq : 0;
     for (int k = 0; k < ODX_MAX_FREQ; ++k) {
@@ -379,6 +385,7 @@ void set_launch_medium(TraceArgs &a, const DevScene &d, bool single)
     a.med.Atau = d.f_Atau;
     a.med.r_out = d.f_r_out;
     a.med.synch = d.f_synch;
+    a.med.spot = d.s.emitter == ODX_EMIT_SPOT;
 }
 
 // Argument checks of odx_render for callers without a context (no message is stored).

@@ -49,6 +49,9 @@ struct DevScene {
     // 1 / Theta_e from f_T_index, f_inv_T0 as for the torus; SynchK in FP32
     float f_inv_kc, f_ky, f_Atau;
     int32_t f_synch;
+    // hot spot: sqrt(r_s^2 + a^2), Omega, the centre's azimuth at emission time 0 for an
+    // image at t_obs (spot_phase + Omega t_obs, reduced mod 2 pi), 4 r_spot
+    float f_spot_Rs, f_spot_om, f_spot_ph, f_spot_R4;
 };
 
 // One scene-table entry for a scene whose rays start at ray_begin (all table builders).
@@ -69,6 +72,7 @@ struct MedConst {
     float nu[ODX_MAX_FREQ], inv_nu3[ODX_MAX_FREQ];
     float inv_kc, ky, Atau, r_out;
     int32_t synch;
+    int32_t spot;  // the launch's scenes are hot spots
 };
 
 struct TraceArgs {

@@ -127,16 +127,6 @@ __device__ inline double nt_disk_planes(const DevScene &S, double *img, double a
 }
 
 // ---- Keplerian hot spot (Section 4.4) -------------------------------------------------------
-__host__ __device__ inline double spot_orbit_radius(const odx_scene &s)
-{
-    return s.spot_r > 0.0 ? s.spot_r : isco_radius(s.a);
-}
-__host__ __device__ inline double spot_omega(const odx_scene &s)
-{
-    const double rs = spot_orbit_radius(s);
-    return 1.0 / (rs * sqrt(rs) + s.a);
-}
-
 // max(d - 4 r_spot, -z) at state y (negative inside the spot) and d.  The photon at y reaches
 // the image plane dt = sgn t later in coordinate time (t runs from 0 there with dt/ds =
 // sgn dt/dlambda), so it left y at t_e = t_obs - sgn t, when the spot centre was at azimuth

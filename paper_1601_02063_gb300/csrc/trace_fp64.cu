@@ -77,28 +77,6 @@ __device__ __noinline__ void locate_crossing64(const Geo<double> &g, const doubl
     for (int i = 0; i < 6; ++i) yc[i] = y5[i];
 }
 
-// First entry into the hot spot inside an accepted step: bisection on the size of a single
-// fifth-order step from the step start (60 halvings), ending inside; returns the state.
-__device__ __noinline__ void locate_spot64(const Geo<double> &g, const odx_scene &s,
-                                           const double y[6], const double k1[6], double h,
-                                           double yc[6])
-{
-    double lo = 0.0, hi = h, dy[6], yt[6], d;
-    for (int it = 0; it < 60; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        ck_geo_increment<double>(g, y, k1, mid, dy);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) yt[i] = y[i] + dy[i];
-        if (spot_region(s, g.sgn, yt, d) < 0.0)
-            hi = mid;
-        else
-            lo = mid;
-    }
-    ck_geo_increment<double>(g, y, k1, hi, dy);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
-}
-
 // For the hot spot, inten carries the Gaussian weight w of the entry point.
 template <int NF>
 __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScene &S,

@@ -388,8 +388,8 @@ __device__ __forceinline__ void near_horizon(float r, float pr, float a, const P
 // (Eq. 2 redshift, Eqs. 30-31).  in = (r, theta, p_r, p_theta, tau_1..tau_NF).
 // Frequency slots past the scene's n_freq repeat its last frequency (never written out).
 // MK, the medium kind of the launch: 0 read per lane from the medium (batched scenes),
-// 1 the torus, 2 the synchrotron shell (single-medium launches: the other emitter's code is
-// not compiled into the stage loop).
+// 1 the torus (or no medium), 2 the synchrotron shell, 3 the hot spot (no medium; its step
+// control and entry test compiled in): single-medium launches carry no other emitter's code.
 template <int NF, int MK, class Med, class Cold>
 __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, float r_isco,
                                          const float *in, const PairStage &ps, const Cold &C,
@@ -501,6 +501,19 @@ __device__ __forceinline__ bool on_crossing(const DevScene &S, RayM<NF> &R, Cold
         return true;
     }
     return false;
+}
+
+// FP32 distance from the hot spot's sphere d = 4 r_spot (the spot test itself and the entry
+// point run in FP64): the centre's azimuth at the emission time t_obs - sgn t.
+__device__ __forceinline__ float spot_gap32(const DevScene &S, float r, float th, float ph,
+                                            float t, float sgn, float a)
+{
+    float sp, cp, ss, cs;
+    sincosf(ph, &sp, &cp);
+    sincosf(S.f_spot_ph - S.f_spot_om * sgn * t, &ss, &cs);
+    const float R = sqrtf(r * r + a * a), z = r * cosf(th);
+    const float dx = R * cp - S.f_spot_Rs * cs, dy = R * sp - S.f_spot_Rs * ss;
+    return sqrtf(dx * dx + dy * dy + z * z) - S.f_spot_R4;
 }
 
 // One FP32 Cash-Karp attempt.  Returns the new status.
@@ -679,6 +692,15 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     // escape: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
     if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
+    if constexpr (MK == 3) {
+        {  // steps near the spot, FP64 within r_spot / 2
+            const float gap = spot_gap32(S, R.yh[0], R.yh[1], R.yh[2], R.yh[3] + C.yl[3][t],
+                                         R.sgnf, R.af);
+            const float sz = 0.25f * S.f_spot_R4;
+            R.hf = fminf(R.hf, fmaxf(0.5f * gap, 0.25f * sz));
+            if (gap < 0.5f * sz) C.r_switch[t] = INFINITY;
+        }
+    }
     C.hsf[t] = R.hf;
     return ODX_RUNNING;
 }
@@ -686,7 +708,7 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 // One FP64 Cash-Karp attempt on the pair state (FP64 tolerance rtol).  The first stage is
 // evaluated afresh in FP64: FP64 steps are rare and batched, and keeping an FP64 first stage
 // alive across the FP32 steps would cost 2 x (6 + 2 NF) registers on every step.
-template <int NF>
+template <int NF, int MK>
 __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, RayM<NF> &R,
                                        ColdM<NF> &C, float r_isco)
 {
@@ -745,6 +767,24 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
         for (int i = 0; i < 6; ++i) df_set(ch[i], cl[i], yc[i]);
         if (on_crossing<NF>(S, R, C, ch, cl)) return ODX_DISK_HIT;
     }
+    if constexpr (MK == 3) {  // first entry into the hot spot
+        double y5[6], d;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) y5[i] = y[i] + dy[i];
+        if (spot_region(S.s, g.sgn, y5, d) < 0.0) {
+            double yc[6];
+            locate_spot64(g, S.s, y, k1, h, yc);
+            spot_region(S.s, g.sgn, yc, d);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                float lo;
+                df_set(R.yh[i], lo, yc[i]);
+                C.yl[i][t] = lo;
+            }
+            df_set(C.Qh[t], C.Ql[t], d);  // the record slot's Q carries d to the finish pass
+            return ODX_DISK_HIT;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         y[i] += dy[i];
@@ -766,6 +806,12 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     // escape test: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
     if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     C.hd[t] = fmin(h_next, S.s.hmax_frac * y[0]);
+    if constexpr (MK == 3) {  // back to FP32 once clear of the spot
+        double d;
+        spot_region(S.s, g.sgn, y, d);
+        C.hd[t] = fmin(C.hd[t], spot_step_cap(S.s, g.sgn, y));
+        if (d - 4.0 * S.s.spot_size > S.s.spot_size) C.r_switch[t] = (float)S.s.r_switch;
+    }
     C.hsd[t] = C.hd[t];
     R.hf = (float)C.hd[t];
     return ODX_RUNNING;
@@ -852,7 +898,7 @@ __global__ void __launch_bounds__(kMixedBlock, MINB)
                 // the FP64 step works on a copy: only this rare path pays for moving the
                 // register state through local memory
                 RayM<NF> r64 = R;
-                status = step64<NF>(A, S, r64, C, R.r_isco);
+                status = step64<NF, MK>(A, S, r64, C, R.r_isco);
                 R = r64;
             } else {
                 if constexpr (SINGLE)
@@ -891,7 +937,13 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     const DevScene &S = A.scenes[find_scene(A, id)];
     const MixedOut o = load80<MixedOut>(A.records + id);
     const double a = A.list_mode ? A.rays[4 * id + 2] : S.s.a;
-    const double L = df_get(o.Lh, o.Ll), Q0 = df_get(o.Qh, o.Ql);
+    const double L = df_get(o.Lh, o.Ll);
+    double Q0 = df_get(o.Qh, o.Ql);
+    double d_spot = 0.0;
+    if (S.s.emitter == ODX_EMIT_SPOT) {  // the slot's Q carries the entry point's d
+        d_spot = Q0;
+        Q0 = init_ray(ray_observer(A, S, id), (S.s.convention == ODX_CONV_LITERAL) ? 1.0 : -1.0).Q;
+    }
     double yend[6];
 #pragma unroll
     for (int i = 0; i < 5; ++i) yend[state_index(i)] = df_get(o.yh[i], o.yl[i]);
@@ -907,7 +959,11 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     r.Q_drift = (carter_q(a, L, yend) - Q0) / fmax(fabs(Q0), 1.0);
     r.r_hit = r.phi_hit = r.g = qnan();
     r.intensity = 0.0;
-    if (o.status == ODX_DISK_HIT) {
+    if (o.status == ODX_DISK_HIT && S.s.emitter == ODX_EMIT_SPOT) {
+        r.r_hit = yend[0];
+        r.phi_hit = yend[2];
+        r.g = spot_redshift(S.s, yend[0], yend[1], L);
+    } else if (o.status == ODX_DISK_HIT) {
         r.r_hit = yend[0];
         r.phi_hit = yend[2];
         r.g = disk_redshift(a, yend[0], L);
@@ -918,8 +974,12 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     if (S.s.emitter == ODX_EMIT_NT_DISK)
         r.intensity = nt_disk_planes(S, img, a, ray_r_isco(A, S, a), r.r_hit, r.g,
                                      o.status == ODX_DISK_HIT);
+    if (S.s.emitter == ODX_EMIT_SPOT) {
+        const double w = S.s.C_norm * exp(-d_spot * d_spot / (2.0 * S.s.spot_size * S.s.spot_size));
+        r.intensity = spot_planes(S, img, w, r.g, o.status == ODX_DISK_HIT);
+    }
     store_record(A.records + id, r);
-    if (img && S.s.emitter != ODX_EMIT_NT_DISK) {
+    if (img && S.s.emitter != ODX_EMIT_NT_DISK && S.s.emitter != ODX_EMIT_SPOT) {
         if (S.s.emitter == ODX_EMIT_TORUS || S.s.emitter == ODX_EMIT_SYNCH) {
             const double Ij = S.s.emitter == ODX_EMIT_SYNCH ? synch_constants(S.s).Aj : 1.0;
             for (int k = 0; k < S.s.n_freq; ++k) {
@@ -949,7 +1009,8 @@ template <int NF>
 cudaError_t launch_mixed_nf(const TraceArgs &args, const odx_launch &L, dim3 grid, cudaStream_t st)
 {
     if constexpr (NF == 0)  // no medium
-        return launch_mixed_nf<NF, true, 1>(args, L, grid, st);
+        return args.med.spot ? launch_mixed_nf<NF, true, 3>(args, L, grid, st)
+                             : launch_mixed_nf<NF, true, 1>(args, L, grid, st);
     else if (!args.single_medium)
         return launch_mixed_nf<NF, false, 0>(args, L, grid, st);
     else

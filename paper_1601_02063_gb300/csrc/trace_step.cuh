@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "kerr_device.cuh"
+#include "trace_common.cuh"
 
 namespace odx {
 
@@ -348,6 +349,28 @@ __device__ __noinline__ void ck_geo_increment(const Geo<T> &g, const T y[6], con
     const MediumT<T> m{};
     T e[6], z[1] = {T(0)}, d1[1], d2[1];
     ck_attempt<T, 0>(g, m, y, k1, z, z, z, h, dy, e, d1, d2);
+}
+
+// First entry into the hot spot inside an accepted step: bisection on the size of a single
+// fifth-order step from the step start (60 halvings), ending inside; returns the state.
+static __device__ __noinline__ void locate_spot64(const Geo<double> &g, const odx_scene &s,
+                                           const double y[6], const double k1[6], double h,
+                                           double yc[6])
+{
+    double lo = 0.0, hi = h, dy[6], yt[6], d;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        ck_geo_increment<double>(g, y, k1, mid, dy);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) yt[i] = y[i] + dy[i];
+        if (spot_region(s, g.sgn, yt, d) < 0.0)
+            hi = mid;
+        else
+            lo = mid;
+    }
+    ck_geo_increment<double>(g, y, k1, hi, dy);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
 }
 
 }  // namespace odx
