@@ -161,3 +161,18 @@ def test_mixed_eight_frequency_hard_case(tracer, orc):
         I_ref = ref["I_nu"][:, k]
         err = np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum()
         assert err <= IMG_ERR, (k, err)
+
+
+def test_mixed_full_size_hard_case_sampled_pixels(tracer, orc):
+    """The 4096^2 hard case (16.8 M rays, 8 frequencies) in the default launch: 300 sampled
+    pixels against the FP64 oracle, per frequency."""
+    sc = W.torus_hard_4096(precision="mixed")
+    got, img = _render(tracer, sc)
+    n = 4096 * 4096
+    pix = W.sample_pixels(n, 300, seed=W.SEED + 7)
+    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])), pixels=pix)
+    same = got["status"][pix] == ref["status"]
+    assert np.mean(same) >= 0.99
+    for k in range(8):
+        rel = _rel(img[k * n + pix][same], ref["I_nu"][same, k])
+        assert np.mean(rel <= 1e-3) >= 0.99 and rel.max() <= 1e-2, (k, rel.max())

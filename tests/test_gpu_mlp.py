@@ -158,10 +158,11 @@ def test_training_on_integrator_rays_reduces_loss(tracer):
         s.close()
 
 
-def test_surrogate_render_with_fallback(tracer):
-    """Short training, then a 128x128 image at a = 0.7, i = 45 deg: fallback pixels carry the
-    integrator's intensities (same tracer, list mode), the others the network's.  Accuracy
-    after full training is measured by the benchmark, not here."""
+@pytest.mark.parametrize("n_side", [128, 2048])
+def test_surrogate_render_with_fallback(tracer, n_side):
+    """Short training, then an image at a = 0.7, i = 45 deg (128^2 and the full 2048^2):
+    fallback pixels carry the integrator's intensities (same tracer, list mode), the others
+    the network's.  Accuracy after full training is measured by the benchmark, not here."""
     import torch
     from paper_1601_02063_gb300.surrogate import Surrogate, image_error
     from paper_1601_02063_gb300 import binding as B
@@ -170,11 +171,11 @@ def test_surrogate_render_with_fallback(tracer):
         x, t = s.make_data(1 << 18)
         s.train(x, t, epochs=8, batch=16384)
         sc = W.surrogate_scene_2048()
-        sc.update(n_alpha=128, n_beta=128)
+        sc.update(n_alpha=n_side, n_beta=n_side)
         img, fb, pix, m = s.render(sc)
         rec_ref, img_ref = tracer.render(sc)
         torch.cuda.synchronize()
-        n = 128 * 128
+        n = n_side * n_side
         assert 0 < m < n
         p = pix[:m].cpu().numpy()
         assert np.all((p >= 0) & (p < n)) and len(np.unique(p)) == m
