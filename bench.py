@@ -145,15 +145,16 @@ def bench_scene(precision: str, size: int = 512) -> dict:
     return sc
 
 
-def cpu_oracle_sample(scene: dict, target_s: float = 12.0):
+def cpu_oracle_sample(scene: dict, target_s: float = 12.0, threads: int = 0):
     """Time the FP64 oracle on a bounded, stratified pixel sample of the workload (every
-    stride-th pixel of every stride-th row), sized to take about target_s seconds."""
+    stride-th pixel of every stride-th row), sized to take about target_s seconds, on
+    `threads` host threads (0: all cores)."""
     import numpy as np
     import oracle
     from paper_1601_02063_gb300 import workloads as W
 
     oracle.build()
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     n = scene["n_alpha"] * scene["n_beta"]
     probe = W.sample_pixels(n, 256, seed=W.SEED + 7)
     sc = dict(scene, precision="fp64")
@@ -635,7 +636,9 @@ def run_ours(args):
         return
     cpu = cpu_oracle_sample(scene) if world == 1 and not args.skip_cpu else None
     if cpu:
+        one = cpu_oracle_sample(scene, target_s=4.0, threads=1)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["single_core"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
