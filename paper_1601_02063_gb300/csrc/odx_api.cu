@@ -22,7 +22,7 @@ using namespace odx;
 struct odx_ctx {
     int device = 0;
     int num_sms = 0;
-    odx_launch launch{128, 3, 32, 1, 16};
+    odx_launch launch{128, 3, 8, 1, 16};  // chunk 8: the queue tail balances (512^2 torus)
     unsigned long long *queue = nullptr;
     DevStats *stats = nullptr;
     DevScene *scenes = nullptr;
@@ -796,7 +796,7 @@ int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, vo
     std::vector<odx_launch> cands;
     if (mixed) {
         for (int bps : {3, 4})
-            for (int chunk : {16, 64})
+            for (int chunk : {8, 16, 64})
                 for (int batch : {8, 16, 24}) cands.push_back({128, bps, chunk, 1, batch});
         cands.push_back({64, 8, 32, 1, 16});
         cands.push_back({128, 4, 32, 0, 16});
