@@ -700,9 +700,14 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
         for (;;) {
             ck_step(&rc, rc.n, y, k1, h, y5, yerr);
             errmax = 0.0;
-            for (int i = 0; i < N_GEO; ++i) errmax = fmax(errmax, fabs(yerr[i] / yscal[i]));
+            int nan_err = 0; /* fmax drops a NaN operand: a NaN component rejects the step */
+            for (int i = 0; i < N_GEO; ++i) {
+                double v = fabs(yerr[i] / yscal[i]);
+                if (isnan(v)) nan_err = 1;
+                errmax = fmax(errmax, v);
+            }
             errmax /= sc->rtol;
-            if (isnan(errmax)) errmax = INFINITY;
+            if (nan_err || isnan(errmax)) errmax = INFINITY;
             if (errmax <= 1.0) break;
             ++n_rej;
             h = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);

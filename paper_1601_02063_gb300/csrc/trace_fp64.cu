@@ -187,13 +187,16 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
 #pragma unroll
             for (int i = 0; i < 6; ++i) y5[i] = R.y[i] + dy[i];
             double errmax = 0.0;
+            bool nan_err = false;  // fmax drops a NaN operand: track it, it rejects the step
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 const double sc = fabs(R.y[i]) + fabs(R.hs * R.k1[i]) + 1e-30;
-                errmax = fmax(errmax, fabs(e[i] / sc));
+                const double v = fabs(e[i] / sc);
+                nan_err |= isnan(v);
+                errmax = fmax(errmax, v);
             }
             errmax /= S.s.rtol;
-            if (isnan(errmax)) errmax = INFINITY;
+            if (nan_err || isnan(errmax)) errmax = INFINITY;
 
             int32_t status = ODX_RUNNING;
             if (errmax <= 1.0) {

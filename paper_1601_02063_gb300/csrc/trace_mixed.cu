@@ -516,6 +516,9 @@ __device__ __forceinline__ float spot_gap32(const DevScene &S, float r, float th
     return sqrtf(dx * dx + dy * dy + z * z) - S.f_spot_R4;
 }
 
+// Attempts after which a ray leaves the FP32 stages for good (typical rays take 100-400).
+constexpr int kFp32Stall = 4096;
+
 // One FP32 Cash-Karp attempt.  Returns the new status.
 //
 // The six stages run as a loop around one inlined right-hand side (one copy of its code in
@@ -641,20 +644,32 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 #undef ODX_SUMS
 
     float errmax = 0.f;
+    bool nan_err = false;  // fmaxf drops a NaN operand: track it, it rejects the step
     const float hs = C.hsf[t];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const float sc = fabsf(R.yh[i]) + fabsf(hs * C.k1[i][t]) + 1e-30f;
-        errmax = fmaxf(errmax, __fdividef(fabsf(hg * e[i]), sc));
+        const float v = __fdividef(fabsf(hg * e[i]), sc);
+        nan_err |= isnan(v);
+        errmax = fmaxf(errmax, v);
     }
     errmax = __fdividef(errmax, S.f_rtol32);
-    if (isnan(errmax)) errmax = INFINITY;
+    if (nan_err || isnan(errmax)) {  // reject; the ray goes on in FP64 steps
+        errmax = INFINITY;
+        C.r_switch[t] = INFINITY;
+    }
     if (!(errmax <= 1.f)) {
         ++C.n_rej[t];
         R.hf = fmaxf(0.9f * h * __powf(errmax, -0.25f), 0.1f * h);
+        // a step that collapses below 1e-6 r (rays passing a pole when the observer sits on
+        // the axis) is beyond the FP32 stages: FP64 steps for the rest of the ray
+        if (R.hf < 1e-6f * R.yh[0]) C.r_switch[t] = INFINITY;
         return R.hf < 1e-12f ? ODX_NUMERR : ODX_RUNNING;
     }
     ++C.n_acc[t];
+    // a ray still in the FP32 stages after kFp32Stall attempts (rays passing a pole when the
+    // observer sits on the axis can creep on at a noise-limited step) finishes in FP64 steps
+    if (C.n_acc[t] + C.n_rej[t] > kFp32Stall) C.r_switch[t] = INFINITY;
     const float h_next = (errmax > 1.89e-4f) ? 0.9f * h * __powf(errmax, -0.2f) : 5.f * h;
 #pragma unroll
     for (int i = 0; i < 6; ++i) dy[i] = __fmul_rn(dy[i], hg);  // rounded before the two-sums
@@ -745,13 +760,16 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     double dy[6], e[6], dtau[NF + 1], dI[NF + 1];
     ck_attempt<double, NF>(g, md, y, k1, tau, kt1, kI1, h, dy, e, dtau, dI);
     double errmax = 0.0;
+    bool nan_err = false;  // fmax drops a NaN operand: track it, it rejects the step
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const double sc = fabs(y[i]) + fabs(C.hsd[t] * k1[i]) + 1e-30;
-        errmax = fmax(errmax, fabs(e[i] / sc));
+        const double v = fabs(e[i] / sc);
+        nan_err |= isnan(v);
+        errmax = fmax(errmax, v);
     }
     errmax /= S.s.rtol;
-    if (isnan(errmax)) errmax = INFINITY;
+    if (nan_err || isnan(errmax)) errmax = INFINITY;
     if (!(errmax <= 1.0)) {
         ++C.n_rej[t];
         C.hd[t] = fmax(0.9 * h * pow(errmax, -0.25), 0.1 * h);

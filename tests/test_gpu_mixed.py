@@ -176,3 +176,26 @@ def test_mixed_full_size_hard_case_sampled_pixels(tracer, orc):
     for k in range(8):
         rel = _rel(img[k * n + pix][same], ref["I_nu"][same, k])
         assert np.mean(rel <= 1e-3) >= 0.99 and rel.max() <= 1e-2, (k, rel.max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("a", [0.5, 0.998])
+@pytest.mark.parametrize("theta_obs", [0.0, math.pi])
+def test_observer_on_the_axis(tracer, orc, theta_obs, a, precision):
+    """Face-on views (theta_obs = 0 or pi, a 9 x 7 window): every ray starts next to a pole and
+    the central one runs along the axis, the coordinate singularity of Boyer-Lindquist where
+    the sin floor of Section 2.1 applies.  Statuses agree with the oracle wherever the
+    oracle's own step control succeeds (it ends a few rays on or beside the axis as NUMERR;
+    those end with some terminal status here); no ray runs out of attempts; disk radii to
+    the path's tolerance."""
+    sc = W.scene(a=a, theta_obs=theta_obs, n_alpha=9, n_beta=7, alpha_min=-9.0, alpha_max=9.0,
+                 beta_min=-7.0, beta_max=7.0, precision=precision)
+    got, _ = _render(tracer, sc)
+    ref = orc.render(dict(sc, precision="fp64"))
+    ok = ref["status"] != 5
+    assert np.all(got["status"][ok] == ref["status"][ok])
+    assert np.all((got["status"] >= 1) & (got["status"] <= 5) & (got["status"] != 4))
+    hit = ok & (ref["status"] == 3)
+    assert hit.sum() > 20
+    tol = 1e-9 if precision == "fp64" else 1e-5
+    assert _rel(got["r_hit"][hit], ref["r_hit"][hit]).max() <= tol
