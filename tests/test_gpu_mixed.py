@@ -199,3 +199,39 @@ def test_observer_on_the_axis(tracer, orc, theta_obs, a, precision):
     assert hit.sum() > 20
     tol = 1e-9 if precision == "fp64" else 1e-5
     assert _rel(got["r_hit"][hit], ref["r_hit"][hit]).max() <= tol
+
+
+def _spin_cases():
+    thin = lambda a, p: W.scene(a=a, n_alpha=32, n_beta=32, precision=p)
+    torus = lambda a, p: dict(W.torus_512(p), a=a, n_alpha=32, n_beta=32)
+    spot = lambda a, p: W.hot_spot(t_obs=13.0, a=a, n=40, precision=p)
+    return [("thin", thin, -0.9), ("thin", thin, 0.9999), ("torus", torus, -0.9),
+            ("spot", spot, -0.6)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(4))
+def test_retrograde_and_near_extremal_spins(tracer, orc, case, precision):
+    """Spin against the disk's rotation (a < 0: r_ISCO beyond 6 M, frame dragging opposed)
+    and a = 0.9999: statuses, disk radii and images against the oracle."""
+    from paper_1601_02063_gb300 import binding as B
+    name, make, a = _spin_cases()[case]
+    sc = make(a, precision)
+    got, img = _render(tracer, sc)
+    ref = orc.render(dict(sc, precision="fp64", **({"C_norm": orc.torus_norm(a)}
+                                                      if name == "torus" else {})))
+    n = sc["n_alpha"] * sc["n_beta"]
+    planes = B.image_planes(sc)
+    I_ref = ref["I_nu"][:, :planes].T.ravel() if name in ("torus", "spot") else ref["intensity"]
+    err = np.abs(img - I_ref).sum() / np.abs(I_ref).sum()
+    hit = (got["status"] == ref["status"]) & (ref["status"] == 3)
+    if precision == "fp64":
+        assert np.all(got["status"] == ref["status"])
+        assert err <= 1e-8
+        if hit.any():
+            assert _rel(got["r_hit"][hit], ref["r_hit"][hit]).max() <= 1e-9
+    else:
+        assert np.mean(got["status"] != ref["status"]) < STATUS_DISAGREE
+        assert err <= IMG_ERR
+        if hit.any():
+            assert _rel(got["r_hit"][hit], ref["r_hit"][hit]).max() <= 1e-4
