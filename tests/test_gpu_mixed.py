@@ -235,3 +235,21 @@ def test_retrograde_and_near_extremal_spins(tracer, orc, case, precision):
         assert err <= IMG_ERR
         if hit.any():
             assert _rel(got["r_hit"][hit], ref["r_hit"][hit]).max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n_freq", [1, 2, 5])
+def test_frequency_counts_that_pad_the_transfer_slots(tracer, orc, n_freq, precision):
+    """Torus images at 1, 2 and 5 frequencies run in kernels compiled for 3 and 8 transfer
+    slots (unused slots repeat the last frequency and are never written out): every plane
+    against the oracle."""
+    sc = W.torus_512(precision)
+    sc.update(n_alpha=24, n_beta=24, freqs=[float(v) for v in np.geomspace(0.5, 2.0, n_freq)])
+    got, img = _render(tracer, sc)
+    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])))
+    n = 24 * 24
+    assert img.size == n_freq * n
+    bar = 1e-9 if precision == "fp64" else IMG_ERR
+    for k in range(n_freq):
+        I_ref = ref["I_nu"][:, k]
+        assert np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum() <= bar, k
