@@ -142,13 +142,19 @@ typedef struct odx_ray_record {
     double H_end, Q_drift;
 } odx_ray_record;
 
-/* Launch shape of the persistent tracing kernels. */
+/* Launch shape of the tracing kernels (the default is {128, 3, 0, 2, 16}). */
 typedef struct odx_launch {
     int32_t block;         /* threads per block, multiple of 32, 32..1024          */
-    int32_t blocks_per_sm; /* resident blocks per SM the grid is sized for (>= 1)  */
-    int32_t chunk;         /* rays a warp takes from the global queue at a time    */
+    int32_t blocks_per_sm; /* resident blocks per SM the grid is sized for and the
+                              register cap of the mixed tracer (2, 3 or 4) (>= 1)   */
+    int32_t chunk;         /* rays a warp takes from the global queue at a time;
+                              0: the tracer's default (mixed 8, FP64 32)          */
     int32_t persistent;    /* 1: persistent warps refilling lanes from the queue;
-                              0: one ray per thread, no queue                       */
+                              0: one ray per thread, no queue; 2 (auto): the mixed
+                              tracer runs launches of 2^19 rays or more one ray per
+                              thread with 4 blocks per SM (3 for more than 3 transfer
+                              slots) and smaller ones persistent; the FP64 tracer
+                              runs persistent                                      */
     int32_t fp64_batch;    /* ODX_MIXED: a warp runs an FP64 step once this many of
                               its lanes wait for one (or no FP32 lane is left), 1..32 */
 } odx_launch;

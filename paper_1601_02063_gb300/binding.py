@@ -178,7 +178,7 @@ def _check(ctx, rc: int, what: str) -> int:
     return rc
 
 
-def odx_set_launch(ctx, block=128, blocks_per_sm=3, chunk=8, persistent=1,
+def odx_set_launch(ctx, block=128, blocks_per_sm=3, chunk=0, persistent=2,
                    fp64_batch=16) -> None:
     L = odx_launch(block, blocks_per_sm, chunk, persistent, fp64_batch)
     _check(ctx, lib().odx_set_launch(ctx, C.byref(L)), "odx_set_launch")

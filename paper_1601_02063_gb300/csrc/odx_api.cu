@@ -22,7 +22,7 @@ using namespace odx;
 struct odx_ctx {
     int device = 0;
     int num_sms = 0;
-    odx_launch launch{128, 3, 8, 1, 16};  // chunk 8: the queue tail balances (512^2 torus)
+    odx_launch launch{128, 3, 0, 2, 16};  // chunk 0 and persistent 2: each tracer's defaults
     unsigned long long *queue = nullptr;
     DevStats *stats = nullptr;
     DevScene *scenes = nullptr;
@@ -493,9 +493,10 @@ int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *L)
         return fail(ctx, ODX_ERR_INVALID_ARG, "block must be a multiple of 32 in 32..1024");
     if (L->blocks_per_sm < 1 || L->blocks_per_sm > 64)
         return fail(ctx, ODX_ERR_INVALID_ARG, "blocks_per_sm must be 1..64");
-    if (L->chunk < 1 || L->chunk > 4096) return fail(ctx, ODX_ERR_INVALID_ARG, "chunk must be 1..4096");
-    if (L->persistent != 0 && L->persistent != 1)
-        return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0 or 1");
+    if (L->chunk < 0 || L->chunk > 4096)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "chunk must be 0 (per-path default) or 1..4096");
+    if (L->persistent < 0 || L->persistent > 2)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0, 1 or 2 (auto)");
     if (L->fp64_batch < 1 || L->fp64_batch > 32)
         return fail(ctx, ODX_ERR_INVALID_ARG, "fp64_batch must be 1..32");
     ctx->launch = *L;

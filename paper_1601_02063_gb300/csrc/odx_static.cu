@@ -117,7 +117,7 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     a.image = image;
     a.queue = reinterpret_cast<unsigned long long *>(base + kQueueOffset);
     a.stats = reinterpret_cast<DevStats *>(base + kStatsOffset);
-    const odx_launch launch{128, 3, 8, 1, 16};
+    const odx_launch launch{128, 3, 0, 2, 16};
     a.chunk = launch.chunk;
     a.persistent = launch.persistent;
     a.fp64_batch = launch.fp64_batch;

@@ -269,9 +269,14 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
     flush_stats(A, lane, my_rays, my_acc, my_rej, 0ull, my_slots, my_active);
 }
 
-cudaError_t launch_trace_fp64(const TraceArgs &args, int32_t nf_slots, const odx_launch &L,
+cudaError_t launch_trace_fp64(const TraceArgs &args_in, int32_t nf_slots, const odx_launch &L_in,
                               int32_t num_sms, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
+    TraceArgs args = args_in;
+    if (args.chunk <= 0) args.chunk = 32;  // the FP64 tracer's default queue chunk
+    odx_launch L = L_in;
+    if (L.persistent == 2) L.persistent = 1;  // "auto": persistent warps for the FP64 tracer
+    args.persistent = L.persistent;
     const dim3 block(L.block);
     const dim3 grid = trace_grid(args, L, num_sms);
     if (ev0) cudaEventRecord(ev0, st);
