@@ -178,6 +178,44 @@ def cpu_oracle_sample(scene: dict, target_s: float = 12.0, threads: int = 0):
             "seconds": dt, "steps": steps, "rays": len(pix)}
 
 
+def cpu_oracle_pixels(scenes, per_scene: int, seed: int):
+    """The FP64 oracle on per_scene seeded pixels of each scene (all host cores): ns per
+    attempted Runge-Kutta step, for the configurations whose full image the oracle would
+    take minutes to hours on."""
+    import oracle
+    from paper_1601_02063_gb300 import workloads as W
+
+    import numpy as np
+
+    oracle.build()
+    threads = oracle.default_threads()
+    if len(scenes) == 1:
+        sc = scenes[0]
+        pix = W.sample_pixels(sc["n_alpha"] * sc["n_beta"], per_scene, seed=seed)
+        t0 = time.perf_counter()
+        res = oracle.render(dict(sc, precision="fp64"), pixels=pix, threads=threads)
+        secs = time.perf_counter() - t0
+    else:
+        # scenes that differ only in spin, inclination and window (a sweep): one ray list
+        lists = []
+        for k, sc in enumerate(scenes):
+            pix = W.sample_pixels(sc["n_alpha"] * sc["n_beta"], per_scene, seed=seed + k)
+            j, i = np.divmod(pix, sc["n_alpha"])
+            al = sc["alpha_min"] + (i + 0.5) * (sc["alpha_max"] - sc["alpha_min"]) / sc["n_alpha"]
+            be = sc["beta_min"] + (j + 0.5) * (sc["beta_max"] - sc["beta_min"]) / sc["n_beta"]
+            lists.append(np.stack([al, be, np.full(len(pix), sc["a"]),
+                                   np.full(len(pix), math.cos(sc["theta_obs"]))], axis=1))
+        rays_l = np.ascontiguousarray(np.concatenate(lists))
+        t0 = time.perf_counter()
+        res = oracle.trace_list(dict(scenes[0], precision="fp64"), rays_l, threads=threads)
+        secs = time.perf_counter() - t0
+    steps = int(res["n_acc"].sum() + res["n_rej"].sum())
+    rays = len(res["n_acc"])
+    return {"value": secs * 1e9 / steps, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{rays} seeded pixels ({per_scene} per scene), {steps} RK steps, "
+                      f"{secs:.2f} s wall"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -347,6 +385,8 @@ def run_ours(args):
                                                            + sts["steps_rejected"]),
                    "lane_refill_efficiency": sts["lane_active"] / max(1, sts["lane_slots"]),
                    "cuda_graph": True, "autotuned_launch": best}
+        if world == 1 and not args.skip_cpu:
+            batched["cpu_oracle"] = cpu_oracle_pixels(sweep, 128, W.SEED + 300)
 
     def timed(fn, reps):
         out = []
@@ -422,6 +462,9 @@ def run_ours(args):
         }
         sg.close()
         del rec2, img2, ref64, out_s
+        if world == 1 and not args.skip_cpu:
+            surrogate["cpu_oracle"] = cpu_oracle_pixels([W.surrogate_scene_2048()], 4096,
+                                                        W.SEED + 500)
 
     # secondary: spectra and a light curve over inclination (Section 4.4): the torus at 16
     # inclinations (5..80 deg), 256^2 each, rendered in one batched launch and reduced to
@@ -611,6 +654,8 @@ def run_ours(args):
                 "steps_per_photon_quantiles_50_90_99_999": qs,
                 "lane_refill_efficiency": sth["lane_active"] / max(1, sth["lane_slots"]),
                 "image_error_vs_fp64_at_512": errs}
+        if world == 1 and not args.skip_cpu:
+            hard["cpu_oracle"] = cpu_oracle_pixels([hsc], 4096, W.SEED + 400)
         del recs, imgs, ref
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
