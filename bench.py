@@ -237,7 +237,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": False,
         "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "image": "512x512", "a": 0.94, "inclination_deg": 30,
+        "config": {"workload": WORKLOAD if args.size == 512 else f"torus{args.size}",
+                   "image": f"{args.size}x{args.size}", "a": 0.94, "inclination_deg": 30,
                    "n_freq": 3, "sample": info["sample"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"],
                          "kind": "oracle", "sample": info["sample"]},
