@@ -196,8 +196,9 @@ int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *launch);
 int32_t odx_get_launch(const odx_ctx *ctx, odx_launch *launch);
 
 /*
- * Render n_scenes images in ONE persistent launch (Section 3: one ray per pixel; the rays of
- * all scenes share one queue).  Per ray: initial state from the image plane (Section 2.2,
+ * Render n_scenes images in ONE launch (Section 3: one ray per pixel; the rays of all scenes
+ * form one index range, handed to warps by a queue or one ray per thread as the launch
+ * shape says, see odx_launch).  Per ray: initial state from the image plane (Section 2.2,
  * Eqs. 18-26, 7, 8, 4, 5, 13), adaptive Cash-Karp integration of the geodesic equations
  * (Section 2.1, Eqs. 4, 5, 9, 12, 14, 15), termination and disk crossing, redshift (Eq. 2)
  * and radiative transfer (Section 2.3, Eqs. 30-31).
