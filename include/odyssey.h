@@ -154,7 +154,7 @@ typedef struct odx_launch {
                               tracer runs launches of 2^19 rays or more one ray per
                               thread with 4 blocks per SM (3 for more than 3 transfer
                               slots) and smaller ones persistent; the FP64 tracer
-                              runs persistent                                      */
+                              from 2^18 rays on one ray per thread                 */
     int32_t fp64_batch;    /* ODX_MIXED: a warp runs an FP64 step once this many of
                               its lanes wait for one (or no FP32 lane is left), 1..32 */
 } odx_launch;
