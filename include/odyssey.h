@@ -148,13 +148,13 @@ typedef struct odx_launch {
     int32_t blocks_per_sm; /* resident blocks per SM the grid is sized for and the
                               register cap of the mixed tracer (2, 3 or 4) (>= 1)   */
     int32_t chunk;         /* rays a warp takes from the global queue at a time;
-                              0: the tracer's default (mixed 8, FP64 32)          */
-    int32_t persistent;    /* 1: persistent warps refilling lanes from the queue;
-                              0: one ray per thread, no queue; 2 (auto): the mixed
-                              tracer runs launches of 2^19 rays or more one ray per
-                              thread with 4 blocks per SM (3 for more than 3 transfer
-                              slots) and smaller ones persistent; the FP64 tracer
-                              from 2^18 rays on one ray per thread                 */
+                              0: the default (32; mixed tracer with persistent 1: 8) */
+    int32_t persistent;    /* 1: persistent warps refilling each finished lane from
+                              the queue; 3: persistent warps that take 32 consecutive
+                              rays once all their lanes are done (warp-coherent
+                              queue); 0: one ray per thread, no queue; 2 (auto): 3,
+                              with 4 blocks per SM for mixed launches of 2^19 rays or
+                              more with up to 3 transfer slots and 3 otherwise      */
     int32_t fp64_batch;    /* ODX_MIXED: a warp runs an FP64 step once this many of
                               its lanes wait for one (or no FP32 lane is left), 1..32 */
 } odx_launch;

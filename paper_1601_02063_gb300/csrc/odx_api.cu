@@ -495,8 +495,8 @@ int32_t odx_set_launch(odx_ctx *ctx, const odx_launch *L)
         return fail(ctx, ODX_ERR_INVALID_ARG, "blocks_per_sm must be 1..64");
     if (L->chunk < 0 || L->chunk > 4096)
         return fail(ctx, ODX_ERR_INVALID_ARG, "chunk must be 0 (per-path default) or 1..4096");
-    if (L->persistent < 0 || L->persistent > 2)
-        return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0, 1 or 2 (auto)");
+    if (L->persistent < 0 || L->persistent > 3)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "persistent must be 0, 1, 2 (auto) or 3");
     if (L->fp64_batch < 1 || L->fp64_batch > 32)
         return fail(ctx, ODX_ERR_INVALID_ARG, "fp64_batch must be 1..32");
     ctx->launch = *L;
@@ -795,16 +795,17 @@ int32_t odx_autotune(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, vo
     }
     const bool mixed = scenes[0].precision == ODX_MIXED;
     std::vector<odx_launch> cands;
-    if (mixed) {
+    if (mixed) {  // warp-coherent queue, refilled lanes, one ray per thread
         for (int bps : {3, 4})
-            for (int chunk : {8, 16, 64})
-                for (int batch : {8, 16, 24}) cands.push_back({128, bps, chunk, 1, batch});
-        cands.push_back({64, 8, 32, 1, 16});
+            for (int batch : {8, 16, 24}) cands.push_back({128, bps, 32, 3, batch});
+        for (int bps : {3, 4})
+            for (int chunk : {8, 16}) cands.push_back({128, bps, chunk, 1, 16});
+        cands.push_back({128, 3, 32, 0, 16});
         cands.push_back({128, 4, 32, 0, 16});
     } else {
-        for (int block : {64, 128})
-            for (int chunk : {16, 64}) cands.push_back({block, 256 / block * 2, chunk, 1, 16});
-        cands.push_back({128, 4, 32, 0, 16});
+        for (int bps : {2, 3}) cands.push_back({128, bps, 32, 3, 16});
+        for (int chunk : {16, 32}) cands.push_back({128, 2, chunk, 1, 16});
+        cands.push_back({128, 2, 32, 0, 16});
     }
     void *rec = nullptr, *img = nullptr;
     ODX_CUDA(ctx, cudaMalloc(&rec, nr * sizeof(odx_ray_record)));

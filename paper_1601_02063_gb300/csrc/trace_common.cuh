@@ -29,6 +29,9 @@ struct WarpQueue {
     {
         id = -1;
         if (exhausted) return;
+        // warp-coherent queue: a warp takes new rays only once all its lanes are done, so its
+        // 32 lanes always trace neighbouring pixels that started together
+        if (A.persistent == 3 && __ballot_sync(kFull, live) != 0u) return;
         if (!A.persistent) {
             const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
             if (!live && t < A.n_total) id = t;

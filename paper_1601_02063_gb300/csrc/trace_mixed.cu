@@ -1041,19 +1041,18 @@ cudaError_t launch_trace_mixed(const TraceArgs &args_in, int32_t nf_slots, const
                                int32_t num_sms, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1)
 {
     TraceArgs args = args_in;
-    if (args.chunk <= 0) args.chunk = 8;  // the mixed tracer's default queue chunk
-    // launch shape "auto": below 2^19 rays persistent warps refilled from the queue (the
-    // queue balances the tail of a small image); above, one ray per thread, so a warp holds
-    // 32 neighbouring pixels that take the same branches together (1024^2 torus 14% faster,
-    // 4096^2 hard case 1.6x), with 4 resident blocks per SM up to 3 transfer slots and 3
-    // above (the 8-slot kernel spills at the 128-register cap)
+    // launch shape "auto": the warp-coherent queue (a warp takes 32 consecutive rays once all
+    // its lanes are done: neighbouring pixels run the same branches together, and the queue
+    // still balances the tail), 4 resident blocks per SM for launches of 2^19 rays or more
+    // with up to 3 transfer slots, 3 otherwise (smaller launches and the 8-slot kernel, which
+    // spills at the 128-register cap)
     odx_launch L = L_in;
     if (L.persistent == 2) {
-        const bool coherent = args.n_total >= (1 << 19);
-        L.persistent = coherent ? 0 : 1;
-        if (coherent) L.blocks_per_sm = nf_slots <= 3 ? 4 : 3;
+        L.persistent = 3;
+        L.blocks_per_sm = (nf_slots <= 3 && args.n_total >= (1 << 19)) ? 4 : 3;
     }
     args.persistent = L.persistent;
+    if (args.chunk <= 0) args.chunk = L.persistent == 3 ? 32 : 8;  // default queue chunk
     if (L.block > 128) return cudaErrorInvalidValue;
     if (args.n_total <= 0) return cudaSuccess;
     const unsigned pass_blocks = (unsigned)((args.n_total + 127) / 128);

@@ -108,7 +108,8 @@ def test_mixed_is_schedule_independent(tracer):
     saved = B.odx_get_launch(tracer.ctx)
     try:
         for launch in (dict(fp64_batch=1, chunk=7), dict(persistent=0, block=64),
-                       dict(fp64_batch=32, chunk=128)):
+                       dict(fp64_batch=32, chunk=128), dict(persistent=1, chunk=8),
+                       dict(persistent=3, chunk=32)):
             tracer.set_launch(**dict(saved, **launch))
             got, _ = _render(tracer, sc)
             assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), launch

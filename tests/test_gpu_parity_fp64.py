@@ -167,7 +167,8 @@ def test_batched_scenes_equal_single_renders(tracer):
 
 @pytest.mark.parametrize("launch", [dict(persistent=0, block=64),
                                     dict(persistent=1, chunk=1, blocks_per_sm=1),
-                                    dict(persistent=1, chunk=256, block=256, blocks_per_sm=1)])
+                                    dict(persistent=1, chunk=256, block=256, blocks_per_sm=1),
+                                    dict(persistent=3, chunk=32, blocks_per_sm=2)])
 def test_launch_shapes_are_bitwise_equal(tracer, launch):
     sc = W.scene(n_alpha=40, n_beta=31)
     base, _ = _render(tracer, sc)
