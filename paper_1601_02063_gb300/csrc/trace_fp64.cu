@@ -1,5 +1,6 @@
-// FP64 backward ray tracer for GB300 (sm_103a): persistent warps that refill finished lanes
-// from a global ray queue, one ray per lane, the whole Runge-Kutta state in registers.
+// FP64 backward ray tracer for GB300 (sm_103a): persistent warps fed from a global ray queue
+// (by default 32 consecutive rays once all lanes of the warp are done, so the warp's lanes
+// trace neighbouring pixels together), one ray per lane, the Runge-Kutta state in registers.
 //
 // Per lane, one loop iteration is exactly one Cash-Karp attempt (Section 2.1: fifth-order
 // Runge-Kutta with adaptive step size), so a rejected step costs its lane one iteration and
@@ -8,7 +9,8 @@
 // right-hand side at the new point, which is both the escape test's dr/ds and the first
 // stage of the next step.  Finished lanes are refilled between iterations: a ballot finds
 // them, one lane takes `chunk` ray indices from the queue with a single atomicAdd, and the
-// indices are handed out by rank within the ballot.
+// indices are handed out by rank within the ballot (with the warp-coherent queue only once
+// the whole warp is done).
 //
 // Radiative transfer (Section 2.3, Eqs. 30-31) rides on the same stages as extra
 // components: the optical depth tau_k needs its stage values (dI/ds depends on exp(-tau)),

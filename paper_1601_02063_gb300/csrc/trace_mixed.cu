@@ -6,9 +6,10 @@
 //   1. init pass (FP64, one ray per thread): initial state and constants of motion
 //      (Section 2.2), horizon and ISCO radii, written into the ray's record slot as float
 //      pairs (hi + lo, ~48-bit);
-//   2. tracer (FP32 hot loop; persistent warps refilled from a queue, or one ray per thread
-//      for large launches): Cash-Karp stages in FP32; the state and
-//      the transfer integrals tau, I kept as float pairs updated with error-free two-sums
+//   2. tracer (FP32 hot loop; persistent warps fed from the ray queue, by default 32
+//      consecutive rays once all lanes of the warp are done): Cash-Karp stages in FP32; the
+//      state and the transfer integrals tau, I kept as float pairs updated with error-free
+//      two-sums
 //      (compensated sums); optional FP64 steps where r < r_switch, run per warp once
 //      `fp64_batch` lanes need one; the final state is written back into the record slot;
 //   3. finish pass (FP64, one ray per thread): null-condition and Carter-constant checks,
