@@ -9,8 +9,7 @@
 //   2. tracer (FP32 hot loop; persistent warps fed from the ray queue, by default 32
 //      consecutive rays once all lanes of the warp are done): Cash-Karp stages in FP32; the
 //      state and the transfer integrals tau, I kept as float pairs updated with error-free
-//      two-sums
-//      (compensated sums); optional FP64 steps where r < r_switch, run per warp once
+//      two-sums (compensated sums); optional FP64 steps where r < r_switch, run per warp once
 //      `fp64_batch` lanes need one; the final state is written back into the record slot;
 //   3. finish pass (FP64, one ray per thread): null-condition and Carter-constant checks,
 //      disk redshift (Eq. 2) and intensity, image in FP64, the final records.
