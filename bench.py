@@ -34,9 +34,9 @@ WORKLOAD = "torus512"
 
 # Algorithmic flops per attempted Runge-Kutta step, counted from the formulas of the
 # method (add, sub, mul, div, sqrt, each transcendental = 1 flop; a fused multiply-add is
-# counted as its two operations).  Derivation in the design doc (per-unit work).
-FLOPS_GEODESIC_STEP = 895.0       # 6 right-hand sides x 90 + stage sums 210 + solution
-                                  # and error 114 + error norm and step control 31
+# counted as its two operations).
+FLOPS_GEODESIC_STEP = 895.0       # 6 right-hand sides x 90 (Eqs. 14-15) + stage sums 210
+                                  # + solution and error 114 + error norm and step control 31
 FLOPS_TORUS_STAGE_BASE = 57.0     # flow, redshift, n_e, T_e per stage
 FLOPS_TORUS_STAGE_PER_NU = 19.0   # per frequency per stage
 FLOPS_RT_SUMS_PER_NU = 54.0       # stage and solution sums of tau, I per frequency
