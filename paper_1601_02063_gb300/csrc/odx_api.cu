@@ -235,7 +235,8 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     a.chunk = ctx->launch.chunk;
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
-    set_launch_medium(a, ctx->host_scenes[0], n_scenes == 1 || list_mode);
+    set_launch_medium(a, ctx->host_scenes[0],
+                      list_mode || shared_medium(ctx->host_scenes.data(), n_scenes));
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
     cudaEvent_t ev0, ev1;
     timing_events(ctx, st, &ev0, &ev1);
@@ -271,9 +272,9 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 }
 
 // Launch the tracer over a scene table already resident on the device (graph capture).
-int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const odx_scene *scenes,
-                        int32_t n_scenes, int64_t n_total, odx_ray_record *records,
-                        double *image, cudaStream_t st)
+int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const DevScene *host_table,
+                        const odx_scene *scenes, int32_t n_scenes, int64_t n_total,
+                        odx_ray_record *records, double *image, cudaStream_t st)
 {
     ODX_CUDA(ctx, cudaMemsetAsync(ctx->queue, 0, sizeof(unsigned long long), st));
     TraceArgs a{};
@@ -289,9 +290,7 @@ int32_t launch_resident(odx_ctx *ctx, const DevScene *dev_table, const odx_scene
     a.chunk = ctx->launch.chunk;
     a.persistent = ctx->launch.persistent;
     a.fp64_batch = ctx->launch.fp64_batch;
-    DevScene d0;
-    fill_dev_scene(d0, scenes[0], 0, 0, 0);
-    set_launch_medium(a, d0, n_scenes == 1);
+    set_launch_medium(a, host_table[0], shared_medium(host_table, n_scenes));
     const int32_t slots = nf_slots(scenes[0].emitter, scenes[0].n_freq);
     cudaEvent_t ev0, ev1;
     timing_events(ctx, st, &ev0, &ev1);
@@ -368,24 +367,43 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
     }
 }
 
+static_assert(sizeof(MedConst) == (11 + 2 * ODX_MAX_FREQ) * 4, "MedConst has no padding");
+
+static MedConst medium_const(const DevScene &d)
+{
+    MedConst m;
+    m.T_index = d.f_T_index;
+    m.inv_T0 = d.f_inv_T0;
+    m.lr_pref = d.f_lr_pref;
+    m.c2_pref = d.f_c2_pref;
+    m.pref0 = d.f_pref0;
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) {
+        m.nu[k] = d.f_nu[k];
+        m.inv_nu3[k] = d.f_inv_nu3[k];
+    }
+    m.inv_kc = d.f_inv_kc;
+    m.ky = d.f_ky;
+    m.Atau = d.f_Atau;
+    m.r_out = d.f_r_out;
+    m.synch = d.f_synch;
+    m.spot = d.s.emitter == ODX_EMIT_SPOT;
+    return m;
+}
+
 void set_launch_medium(TraceArgs &a, const DevScene &d, bool single)
 {
     a.single_medium = single ? 1 : 0;
-    a.med.T_index = d.f_T_index;
-    a.med.inv_T0 = d.f_inv_T0;
-    a.med.lr_pref = d.f_lr_pref;
-    a.med.c2_pref = d.f_c2_pref;
-    a.med.pref0 = d.f_pref0;
-    for (int k = 0; k < ODX_MAX_FREQ; ++k) {
-        a.med.nu[k] = d.f_nu[k];
-        a.med.inv_nu3[k] = d.f_inv_nu3[k];
+    a.med = medium_const(d);
+}
+
+bool shared_medium(const DevScene *table, int32_t n_scenes)
+{
+    const MedConst m0 = medium_const(table[0]);
+    for (int32_t k = 1; k < n_scenes; ++k) {
+        const MedConst mk = medium_const(table[k]);
+        if (memcmp(&mk, &m0, sizeof(MedConst)) != 0) return false;
     }
-    a.med.inv_kc = d.f_inv_kc;
-    a.med.ky = d.f_ky;
-    a.med.Atau = d.f_Atau;
-    a.med.r_out = d.f_r_out;
-    a.med.synch = d.f_synch;
-    a.med.spot = d.s.emitter == ODX_EMIT_SPOT;
+    return true;
 }
 
 // Argument checks of odx_render for callers without a context (no message is stored).
@@ -742,7 +760,8 @@ int32_t odx_graph_create(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = launch_resident(ctx, g->table, scenes, n_scenes, ray, records, image, cap);
+        rc = launch_resident(ctx, g->table, table.data(), scenes, n_scenes, ray, records, image,
+                             cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         g->graph = graph;

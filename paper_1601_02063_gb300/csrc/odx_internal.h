@@ -94,6 +94,10 @@ struct TraceArgs {
 
 // Fill a.single_medium and a.med from the host copy of scene 0.
 void set_launch_medium(TraceArgs &a, const DevScene &scene0, bool single);
+// True when every scene of the table folds to the same medium constants, bit for bit: the
+// launch can then take the single-medium kernels (constants in the kernel parameters, the
+// medium kind compiled in), which compute each ray as the per-lane-medium kernels do.
+bool shared_medium(const DevScene *table, int32_t n_scenes);
 
 // Launch the FP64 or mixed tracer (with its passes) on `stream`; when ev0/ev1 are given,
 // they are recorded immediately before and after the tracing kernel itself.

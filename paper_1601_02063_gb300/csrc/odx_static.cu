@@ -121,7 +121,7 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     a.chunk = launch.chunk;
     a.persistent = launch.persistent;
     a.fp64_batch = launch.fp64_batch;
-    odx::set_launch_medium(a, table[0], n_scenes == 1);
+    odx::set_launch_medium(a, table[0], odx::shared_medium(table, n_scenes));
     const int32_t slots = odx::transfer_slots(scenes[0].emitter, scenes[0].n_freq);
     const cudaError_t e =
         scenes[0].precision == ODX_MIXED

@@ -150,12 +150,16 @@ __device__ inline double spot_region(const odx_scene &s, double sgn, const doubl
 }
 
 // Step cap near the spot: no step may carry a ray across it unseen, |h| <= (d - 4 r_spot) / 2,
-// but not below r_spot / 4.
+// but not below r_spot / 4 (d from spot_region).
+__device__ __forceinline__ double spot_cap(const odx_scene &s, double d)
+{
+    return fmax(0.5 * (d - 4.0 * s.spot_size), 0.25 * s.spot_size);
+}
 __device__ inline double spot_step_cap(const odx_scene &s, double sgn, const double y[6])
 {
     double d;
     spot_region(s, sgn, y, d);
-    return fmax(0.5 * (d - 4.0 * s.spot_size), 0.25 * s.spot_size);
+    return spot_cap(s, d);
 }
 
 // Redshift of gas co-rotating with the spot centre at Omega at (r, theta): g = 1 / (u^t

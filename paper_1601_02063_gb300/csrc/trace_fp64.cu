@@ -220,11 +220,11 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         status = ODX_DISK_HIT;
                     }
                 }
-                double d_spot;
+                double d_spot = 0.0;  // spot distance at y5, the step's end (hot spot)
                 if (status == ODX_RUNNING && S.s.emitter == ODX_EMIT_SPOT &&
                     spot_region(S.s, R.sgn, y5, d_spot) < 0.0) {  // first entry into the spot
                     double yc[6];
-                    locate_spot64(g, S.s, R.y, R.k1, h, yc);
+                    locate_spot64(g, S.s, R.y, R.k1, h, yc, 60);
                     spot_region(S.s, R.sgn, yc, d_spot);
                     const double w = S.s.C_norm * exp(-d_spot * d_spot /
                                                       (2.0 * S.s.spot_size * S.s.spot_size));
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                     }
                     R.h = fmin(h_next, S.s.hmax_frac * R.y[0]);
                     if (S.s.emitter == ODX_EMIT_SPOT)
-                        R.h = fmin(R.h, spot_step_cap(S.s, R.sgn, R.y));
+                        R.h = fmin(R.h, spot_cap(S.s, d_spot));  // R.y is y5
                     R.hs = R.h;
                 }
             } else {

@@ -708,14 +708,12 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     // escape: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
     if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     R.hf = fminf(h_next, S.f_hmax_frac * R.yh[0]);
-    if constexpr (MK == 3) {
-        {  // steps near the spot, FP64 within r_spot / 2
-            const float gap = spot_gap32(S, R.yh[0], R.yh[1], R.yh[2], R.yh[3] + C.yl[3][t],
-                                         R.sgnf, R.af);
-            const float sz = 0.25f * S.f_spot_R4;
-            R.hf = fminf(R.hf, fmaxf(0.5f * gap, 0.25f * sz));
-            if (gap < 0.5f * sz) C.r_switch[t] = INFINITY;
-        }
+    if constexpr (MK == 3) {  // steps near the spot, FP64 within r_spot / 2
+        const float gap = spot_gap32(S, R.yh[0], R.yh[1], R.yh[2], R.yh[3] + C.yl[3][t], R.sgnf,
+                                     R.af);
+        const float sz = 0.25f * S.f_spot_R4;
+        R.hf = fminf(R.hf, fmaxf(0.5f * gap, 0.25f * sz));
+        if (gap < 0.5f * sz) C.r_switch[t] = INFINITY;
     }
     C.hsf[t] = R.hf;
     return ODX_RUNNING;
@@ -786,13 +784,17 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
         for (int i = 0; i < 6; ++i) df_set(ch[i], cl[i], yc[i]);
         if (on_crossing<NF>(S, R, C, ch, cl)) return ODX_DISK_HIT;
     }
+    double spot_d = 0.0;  // distance from the spot's centre at the step's end
     if constexpr (MK == 3) {  // first entry into the hot spot
         double y5[6], d;
 #pragma unroll
         for (int i = 0; i < 6; ++i) y5[i] = y[i] + dy[i];
-        if (spot_region(S.s, g.sgn, y5, d) < 0.0) {
+        const double q5 = spot_region(S.s, g.sgn, y5, spot_d);
+        if (q5 < 0.0) {
             double yc[6];
-            locate_spot64(g, S.s, y, k1, h, yc);
+            // the entry point to 4e-9 r_spot (the FP64 path bisects to 2^-60 of the step;
+            // both are far inside the reduced-precision intensity bar)
+            enter_spot64(g, S.s, y, k1, h, q5, 4e-9 * S.s.spot_size, yc);
             spot_region(S.s, g.sgn, yc, d);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -825,11 +827,9 @@ __device__ __noinline__ int32_t step64(const TraceArgs &A, const DevScene &S, Ra
     // escape test: dr/ds = sgn Delta p_r / Sigma has the sign of sgn p_r outside the horizon
     if (R.sgnf * R.yh[4] > 0.f && R.yh[0] > C.r_start[t]) return ODX_ESCAPED;
     C.hd[t] = fmin(h_next, S.s.hmax_frac * y[0]);
-    if constexpr (MK == 3) {  // back to FP32 once clear of the spot
-        double d;
-        spot_region(S.s, g.sgn, y, d);
-        C.hd[t] = fmin(C.hd[t], spot_step_cap(S.s, g.sgn, y));
-        if (d - 4.0 * S.s.spot_size > S.s.spot_size) C.r_switch[t] = (float)S.s.r_switch;
+    if constexpr (MK == 3) {  // back to FP32 once clear of the spot (y is y5)
+        C.hd[t] = fmin(C.hd[t], spot_cap(S.s, spot_d));
+        if (spot_d - 4.0 * S.s.spot_size > S.s.spot_size) C.r_switch[t] = (float)S.s.r_switch;
     }
     C.hsd[t] = C.hd[t];
     R.hf = (float)C.hd[t];

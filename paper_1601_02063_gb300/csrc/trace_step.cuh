@@ -352,13 +352,14 @@ __device__ __noinline__ void ck_geo_increment(const Geo<T> &g, const T y[6], con
 }
 
 // First entry into the hot spot inside an accepted step: bisection on the size of a single
-// fifth-order step from the step start (60 halvings), ending inside; returns the state.
+// fifth-order step from the step start (the given number of halvings), ending inside;
+// returns the state.
 static __device__ __noinline__ void locate_spot64(const Geo<double> &g, const odx_scene &s,
                                            const double y[6], const double k1[6], double h,
-                                           double yc[6])
+                                           double yc[6], int halvings)
 {
     double lo = 0.0, hi = h, dy[6], yt[6], d;
-    for (int it = 0; it < 60; ++it) {
+    for (int it = 0; it < halvings; ++it) {
         const double mid = 0.5 * (lo + hi);
         ck_geo_increment<double>(g, y, k1, mid, dy);
 #pragma unroll
@@ -367,6 +368,45 @@ static __device__ __noinline__ void locate_spot64(const Geo<double> &g, const od
             hi = mid;
         else
             lo = mid;
+    }
+    ck_geo_increment<double>(g, y, k1, hi, dy);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) yc[i] = y[i] + dy[i];
+}
+
+// The same entry point by the Illinois variant of regula falsi on q(s), the spot region
+// value (a distance in M) after a single fifth-order step of size s from the step start:
+// q(0) > 0 outside, q(h) = q_end < 0 inside.  The bracket [lo, hi] always keeps hi inside;
+// the search stops once q(hi) >= -tol (at most 40 evaluations) and returns the state at hi.
+// The secant uses the Illinois weights (the value at an end kept twice in a row is halved);
+// a secant point outside the open bracket falls back to the midpoint.
+static __device__ __noinline__ void enter_spot64(const Geo<double> &g, const odx_scene &s,
+                                          const double y[6], const double k1[6], double h,
+                                          double q_end, double tol, double yc[6])
+{
+    double dy[6], yt[6], d;
+    double lo = 0.0, hi = h;
+    double flo = spot_region(s, g.sgn, y, d), fhi = q_end;  // secant weights
+    double q_hi = q_end;                                   // q at hi itself
+    int side = 0;
+    for (int it = 0; it < 40 && q_hi < -tol; ++it) {
+        double m = (lo * fhi - hi * flo) / (fhi - flo);
+        if (!(m > lo && m < hi)) m = 0.5 * (lo + hi);
+        ck_geo_increment<double>(g, y, k1, m, dy);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) yt[i] = y[i] + dy[i];
+        const double qm = spot_region(s, g.sgn, yt, d);
+        if (qm < 0.0) {
+            hi = m;
+            fhi = q_hi = qm;
+            if (side == -1) flo *= 0.5;
+            side = -1;
+        } else {
+            lo = m;
+            flo = qm;
+            if (side == 1) fhi *= 0.5;
+            side = 1;
+        }
     }
     ck_geo_increment<double>(g, y, k1, hi, dy);
 #pragma unroll

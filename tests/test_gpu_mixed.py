@@ -254,3 +254,25 @@ def test_frequency_counts_that_pad_the_transfer_slots(tracer, orc, n_freq, preci
     for k in range(n_freq):
         I_ref = ref["I_nu"][:, k]
         assert np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum() <= bar, k
+
+
+def test_batched_media_select_the_right_kernel(tracer):
+    """A batch whose scenes fold to the same medium constants (the torus at two inclinations)
+    runs the single-medium kernel and reproduces single-scene launches bit for bit; a batch
+    whose media differ (two electron temperatures) runs the per-lane-medium kernel and agrees
+    with single-scene launches within a tenth of the mixed-path image bar."""
+    base = dict(W.torus_512("mixed"), n_alpha=24, n_beta=20)
+    shared = [dict(base, theta_obs=0.5), dict(base, theta_obs=1.2)]
+    differ = [dict(base, T0=10.0), dict(base, T0=20.0)]
+    n = 24 * 20
+    for scenes, exact in ((shared, True), (differ, False)):
+        both, img = _render(tracer, scenes)
+        for k, sc in enumerate(scenes):
+            one, img1 = _render(tracer, sc)
+            part, ipart = both[k * n:(k + 1) * n], img[3 * k * n:3 * (k + 1) * n]
+            if exact:
+                assert np.array_equal(part.view(np.uint8), one.view(np.uint8))
+                assert np.array_equal(ipart, img1, equal_nan=True)
+            else:
+                assert np.mean(part["status"] == one["status"]) >= 0.99
+                assert np.abs(ipart - img1).sum() / np.abs(img1).sum() < 0.1 * IMG_ERR

@@ -222,6 +222,27 @@ def test_invalid_arguments_are_rejected(tracer, bad):
     assert torch.all(rec == 7.0)  # outputs untouched
 
 
+@pytest.mark.parametrize("base,bad", [("synch", dict(n_e0=0.0)), ("synch", dict(beta_B=float("nan"))),
+                                      ("synch", dict(mass=-1.0)), ("synch", dict(r_out=0.0)),
+                                      ("spot", dict(spot_size=0.0)), ("spot", dict(C_norm=-1.0)),
+                                      ("spot", dict(t_obs=float("inf")))])
+def test_invalid_emitter_parameters_are_rejected(tracer, base, bad):
+    """The same scene renders without the bad parameter, so the rejection is the parameter's."""
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    sc = W.synch_shell(n=4) if base == "synch" else W.hot_spot(n=4)
+    rec = torch.full((16, 10), 7.0, dtype=torch.float64, device="cuda")
+    assert B.odx_render(tracer.ctx, [sc], rec.data_ptr(), None, None, check=False) == B.OK
+    torch.cuda.synchronize()
+    rec.fill_(7.0)
+    sc.update(bad)
+    rc = B.odx_render(tracer.ctx, [sc], rec.data_ptr(), None, None, check=False)
+    assert rc == B.ERR_INVALID_ARG
+    assert B.odx_last_error(tracer.ctx)
+    torch.cuda.synchronize()
+    assert torch.all(rec == 7.0)
+
+
 def test_misaligned_records_rejected(tracer):
     import torch
     from paper_1601_02063_gb300 import binding as B

@@ -56,6 +56,18 @@ def test_fp64_shell_matches_oracle(tracer, orc, a):
         assert I_ref.max() > 0 and np.all(I_got >= 0)
 
 
+def test_spin_batch_equals_single_renders(tracer):
+    """Shells that differ only in spin fold to the same medium constants: one mixed launch of
+    both gives exactly the records and image planes of two single-scene launches."""
+    scenes = [dict(W.synch_shell(a=a), n_alpha=24, n_beta=20) for a in (0.0, 0.9)]
+    both, img = _render(tracer, scenes)
+    n = 24 * 20
+    for k, sc in enumerate(scenes):
+        one, img1 = _render(tracer, sc)
+        assert np.array_equal(both[k * n:(k + 1) * n].view(np.uint8), one.view(np.uint8))
+        assert np.array_equal(img[3 * k * n:3 * (k + 1) * n], img1, equal_nan=True)
+
+
 @pytest.mark.parametrize("a", [0.0, 0.998])
 def test_mixed_shell_image_error(tracer, orc, a):
     sc = W.synch_shell(a=a, n=48, precision="mixed")
