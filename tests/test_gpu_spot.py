@@ -95,7 +95,8 @@ def test_spot_image_repeats_after_one_period(tracer, orc):
 @pytest.mark.parametrize("a,t_obs", [(0.0, 20.0), (0.9, 61.0)])
 def test_mixed_spot_matches_oracle(tracer, orc, a, t_obs):
     """Mixed path: the FP32 steps approach the spot and hand over to FP64 steps within
-    r_spot / 2 of it, which find the entry point as the FP64 path does.  A ray that grazes
+    r_spot / 2 of it, which find the entry point (regula falsi to 4e-9 r_spot where the FP64
+    path bisects to 2^-60 of the step).  A ray that grazes
     the spot along a chord shorter than the step floor (r_spot / 4) can be seen or missed
     by either step sequence, so silhouette pixels may differ in status (bounded below);
     intensities are compared where the statuses agree."""
