@@ -220,9 +220,21 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         status = ODX_DISK_HIT;
                     }
                 }
-                double d_spot = 0.0;  // spot distance at y5, the step's end (hot spot)
-                if (status == ODX_RUNNING && S.s.emitter == ODX_EMIT_SPOT &&
-                    spot_region(S.s, R.sgn, y5, d_spot) < 0.0) {  // first entry into the spot
+                // hot spot: d_spot is the distance from the spot's centre at y5, the step's
+                // end.  It stays infinite where the lower bound d >= |sqrt(r^2 + a^2) - R_s|
+                // (two points at those cylindrical radii are at least that far apart) keeps
+                // y5 outside the spot and the step cap from binding: there the exact
+                // distance changes nothing and its three FP64 sincos are skipped.
+                double d_spot = INFINITY;
+                bool near_spot = false;
+                if (status == ODX_RUNNING && S.s.emitter == ODX_EMIT_SPOT) {
+                    const double Rs = (double)S.f_spot_Rs;  // FP32-rounded: 1e-6 margin
+                    const double d_low =
+                        fabs(sqrt(y5[0] * y5[0] + S.s.a * S.s.a) - Rs) - 1e-6 * Rs;
+                    near_spot = 0.5 * (d_low - 4.0 * S.s.spot_size) <
+                                fmin(h_next, S.s.hmax_frac * y5[0]);
+                }
+                if (near_spot && spot_region(S.s, R.sgn, y5, d_spot) < 0.0) {  // first entry
                     double yc[6];
                     locate_spot64(g, S.s, R.y, R.k1, h, yc, 60);
                     spot_region(S.s, R.sgn, yc, d_spot);
