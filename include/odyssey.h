@@ -67,7 +67,8 @@ extern "C" {
                                 emissivity integrates over directions: the transfer uses
                                 j_nu / 4 pi per steradian */
 #define ODX_EMIT_SPOT 5      /* optically thick Keplerian hot spot (Section 4.4); the mixed
-                                path takes FP64 steps within r_spot / 2 of it: the centre orbits the equatorial circle r = spot_r
+                                path takes FP64 steps within r_spot / 2 of it.  The centre
+                                orbits the equatorial circle r = spot_r
                                 (<= 0: r_ISCO) at Omega = 1/(r^1.5 + a), azimuth spot_phase +
                                 Omega t; a photon seen at t_obs left its point at t_obs - dt
                                 (dt: coordinate time along the ray); the spot is d < 4
