@@ -23,6 +23,7 @@ MAX_FREQ = 8
 STATUS = {"running": 0, "escaped": 1, "captured": 2, "disk_hit": 3, "maxsteps": 4, "numerr": 5}
 EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "const": 3, "nt_disk": 4, "synch": 5, "spot": 6}
 CONVENTIONS = {"physical": 0, "literal": 1}
+RT_CONTROL = {"controlled": 0, "ride": 1}
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +58,7 @@ class Scene(C.Structure):
         ("n_e0", C.c_double), ("beta_B", C.c_double), ("mass", C.c_double),
         ("spot_r", C.c_double), ("spot_size", C.c_double), ("spot_phase", C.c_double),
         ("t_obs", C.c_double),
+        ("rt_control", C.c_int32), ("pad_", C.c_int32),
     ]
 
 
@@ -144,6 +146,7 @@ def make_scene(d: dict) -> Scene:
         sc.freqs[i] = float(f)
     sc.max_steps = int(d["max_steps"])
     sc.convention = CONVENTIONS[d.get("convention", "physical")]
+    sc.rt_control = RT_CONTROL[d.get("rt_control", "controlled")]
     sc.n_e0 = float(d.get("n_e0", 0.0))
     sc.beta_B = float(d.get("beta_B", 0.0))
     sc.mass = float(d.get("mass", 0.0))

@@ -481,9 +481,32 @@ static void torus_flow(double a, double r_isco, double r, double sint, double co
 typedef struct {
     const orc_scene *sc;
     double a, L, sgn, r_isco, r_horizon;
+    double r_stop; /* the ray stops inside this radius; the medium ends there too */
     int n; /* number of integrated components: 6 geodesic + 2 per frequency (RT) */
     int n_rt;
+    double I_floor[ORC_MAX_FREQ]; /* error-scale floor of each invariant intensity */
 } ray_ctx;
+
+/* reading: the invariant intensities of the transfer equation are under the step control
+ * (the paper integrates Eqs. 30-31 along with the geodesic and names no error norm for
+ * them).  Each I_k enters the error norm with the scale |I_k| + |h dI_k/ds| + I_floor_k,
+ * I_floor_k = RT_FLOOR_FRAC times the source function of the medium at its temperature
+ * scale T0 seen at nu_k, B_nu(T0) / nu^3 (the test medium: its source function eps /
+ * kappa), so that emission far below the medium's own intensity scale does not set the
+ * step.  tau_k stays out of the norm: its error reaches I_k only through exp(-tau_k), which
+ * the estimate of I_k already carries.  With the transfer components outside the norm
+ * (ORC_RT_RIDE, the earlier reading) the steps follow the geodesic alone and the
+ * intensities of rays through steep emission (the shadow's edge of the torus, the inner
+ * synchrotron shell) are good to 1e-3 - 1e-2 only, even at rtol 1e-8. */
+#define RT_FLOOR_FRAC 3e-5
+
+static double source_scale(const orc_scene *sc, double nu)
+{
+    if (sc->emitter == ORC_EMIT_CONST) return sc->T0 / sc->C_norm;
+    if (sc->emitter == ORC_EMIT_SYNCH)
+        return 2.0 * CGS_H / (CGS_C * CGS_C) / expm1(CGS_H * nu / (sc->T0 * CGS_ME * CGS_C * CGS_C));
+    return 2.0 / expm1(nu / sc->T0); /* torus: B_nu(T) = 2 nu^3 / (exp(nu / T) - 1) */
+}
 
 /* dy/ds for the geodesic and, for RT emitters, Eqs. 30-31 per frequency:
  *   dtau/ds = alpha_0(nu_0) / g,   dI/ds = j_0(nu_0) / (g nu_0^3) exp(-tau),
@@ -495,6 +518,14 @@ static void derivs(const ray_ctx *rc, int n, const double *y, double *dy)
     orc_geodesic_rhs(rc->a, rc->L, y, f);
     for (int i = 0; i < N_GEO; ++i) dy[i] = rc->sgn * f[i];
     if (rc->n_rt == 0 || n == N_GEO) return;
+    /* reading: rays stop at r < horizon_factor r_+, and the medium ends there: no emission
+     * or absorption inside that radius.  The last step of a captured ray ends somewhere
+     * inside it, at a radius that depends on the step sequence; without this the intensity
+     * of such rays would depend on that step. */
+    if (y[0] < rc->r_stop) {
+        for (int k = 0; k < rc->n_rt; ++k) dy[N_GEO + 2 * k] = dy[N_GEO + 2 * k + 1] = 0.0;
+        return;
+    }
 
     const orc_scene *sc = rc->sc;
     if (sc->emitter == ORC_EMIT_CONST) {
@@ -650,6 +681,9 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
                   ? sc->n_freq
                   : 0;
     rc.n = N_GEO + 2 * rc.n_rt;
+    rc.r_stop = sc->horizon_factor * rc.r_horizon;
+    for (int k = 0; k < rc.n_rt; ++k)
+        rc.I_floor[k] = RT_FLOOR_FRAC * source_scale(sc, sc->freqs[k]);
 
     double y[N_MAX], Q0, L;
     memset(y, 0, sizeof(y));
@@ -658,7 +692,7 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
 
     double r_in = (sc->r_in > 0.0) ? sc->r_in : rc.r_isco;
     double r_start = y[0];
-    double r_stop = sc->horizon_factor * rc.r_horizon;
+    double r_stop = rc.r_stop;
 
     memset(out, 0, sizeof(*out));
     out->r_cross = out->phi_cross = NAN;
@@ -670,7 +704,7 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
     int status = ORC_RUNNING;
     int n_acc = 0, n_rej = 0, n_cross = 0;
     double h = sc->h0, s = 0.0;
-    double k1[N_MAX], y5[N_MAX], yerr[N_MAX], yscal[N_GEO], dy[N_MAX];
+    double k1[N_MAX], y5[N_MAX], yerr[N_MAX], yscal[N_GEO + ORC_MAX_FREQ], dy[N_MAX];
     int np = 0;
     if (s_pts && np < max_pts) {
         s_pts[np] = s;
@@ -695,6 +729,10 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
         }
         derivs(&rc, rc.n, y, k1);
         for (int i = 0; i < N_GEO; ++i) yscal[i] = fabs(y[i]) + fabs(h * k1[i]) + 1e-30;
+        for (int k = 0; k < rc.n_rt; ++k) {
+            int iI = N_GEO + 2 * k + 1;
+            yscal[N_GEO + k] = fabs(y[iI]) + fabs(h * k1[iI]) + rc.I_floor[k];
+        }
 
         double errmax;
         for (;;) {
@@ -705,6 +743,14 @@ static int trace_core(const orc_scene *sc, double alpha, double beta, orc_result
                 double v = fabs(yerr[i] / yscal[i]);
                 if (isnan(v)) nan_err = 1;
                 errmax = fmax(errmax, v);
+            }
+            if (sc->rt_control == ORC_RT_CONTROLLED) {
+                for (int k = 0; k < rc.n_rt; ++k) {
+                    int iI = N_GEO + 2 * k + 1;
+                    double v = fabs(yerr[iI] / yscal[N_GEO + k]);
+                    if (isnan(v)) nan_err = 1;
+                    errmax = fmax(errmax, v);
+                }
             }
             errmax /= sc->rtol;
             if (nan_err || isnan(errmax)) errmax = INFINITY;

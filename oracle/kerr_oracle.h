@@ -40,6 +40,10 @@
 #define ORC_EMIT_SYNCH 5     /* Keplerian shell, thermal synchrotron (Section 4.5, CGS) */
 #define ORC_EMIT_SPOT 6      /* optically thick Keplerian hot spot (Section 4.4)       */
 
+/* step control of the transfer components */
+#define ORC_RT_CONTROLLED 0 /* invariant intensities in the error norm (default)        */
+#define ORC_RT_RIDE 1       /* geodesic components only; tau and I ride on its steps   */
+
 /* sign conventions for the traced photon (see the direction reading in the design notes) */
 #define ORC_CONV_PHYSICAL 0 /* real outgoing photon, traced back in affine time */
 #define ORC_CONV_LITERAL 1  /* future-directed inward photon, Eqs. 24-26 as printed */
@@ -67,6 +71,11 @@ typedef struct {
      * azimuth spot_phase + Omega t; Gaussian width spot_size (r_spot); the image is the one
      * seen at observer time t_obs; emitted I_nu = C_norm exp(-d^2 / (2 r_spot^2)) B_nu(T0) */
     double spot_r, spot_size, spot_phase, t_obs;
+    /* step control of the transfer equation (torus, shell, test medium): ORC_RT_CONTROLLED
+     * puts the invariant intensities into the error norm; ORC_RT_RIDE leaves them out (they
+     * ride on the geodesic's steps) */
+    int32_t rt_control;
+    int32_t pad_;
 } orc_scene;
 
 typedef struct {

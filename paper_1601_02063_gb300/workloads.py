@@ -27,6 +27,9 @@ _DEFAULTS = dict(
     ne_index=1.5, theta_width=0.3, T0=10.0, T_index=0.84, C_norm=None, nu_norm=1.0,
     rtol=1e-8, h0=1.0, hmax_frac=0.1, horizon_factor=1.01, max_steps=100000,
     convention="physical", precision="fp64",
+    # transfer components under the step control ("controlled") or riding on the geodesic's
+    # steps ("ride")
+    rt_control="controlled",
     # reduced-precision controls (ignored by the FP64 path)
     rtol_fp32=1e-6, r_switch=0.0,
     # synchrotron shell: n_e at r = 1 [cm^-3], field parameter beta_B, mass [M_sun]
@@ -98,15 +101,12 @@ def synch_shell(a: float = 0.0, n: int = 256, precision: str = "mixed",
     black hole seen at i = 60 deg: n_e = 3e7 r^-1.1 cm^-3, Theta_e = 100 r^-0.84, field from
     B^2 / 8 pi = n_e m_p c^2 / (6 beta_B r) with beta_B = 10, shell out to 500 M, images
     at 150, 340 and 1000 GHz over +-15 M (optical depth through the shell about 6, 1 and
-    0.1).  Steps are capped at 0.05 r: the transfer terms are not under step control and
-    the 1000 GHz emissivity, exp(-1.8899 x^1/3) with x ~ r^2.7, changes by a factor ~2 per
-    0.1 r step near the hole (image error of the integration ~5e-4 at 0.05 r, ~1e-3 at
-    0.1 r)."""
+    0.1).  The 1000 GHz emissivity, exp(-1.8899 x^1/3) with x ~ r^2.7, changes by a factor
+    ~2 per 0.1 r step near the hole; the intensities' step control resolves it."""
     return scene(a=a, theta_obs=math.radians(60.0), alpha_min=-15.0, alpha_max=15.0,
                  beta_min=-15.0, beta_max=15.0, n_alpha=n, n_beta=n, emitter="synch",
                  freqs=list(freqs), r_out=500.0, ne_index=1.1, theta_width=10.0, T0=100.0,
-                 T_index=0.84, n_e0=3e7, beta_B=10.0, mass=4e6, hmax_frac=0.05,
-                 precision=precision)
+                 T_index=0.84, n_e0=3e7, beta_B=10.0, mass=4e6, precision=precision)
 
 
 def hot_spot(t_obs: float = 0.0, a: float = 0.0, n: int = 128, precision: str = "fp64") -> dict:

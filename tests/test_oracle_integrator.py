@@ -219,24 +219,61 @@ def test_isco_bounds_disk_hits(orc):
 
 def test_constant_medium_closed_form(orc):
     """Eqs. 30-31 with constant coefficients dtau/ds = kappa, dI/ds = eps exp(-tau) integrate to
-    tau = kappa s, I = (eps / kappa)(1 - exp(-kappa s)) over the traced affine length s.
-    The transfer components ride on the geodesic's steps (they are outside step control),
-    so their error is the fifth-order truncation in kappa h: doubling kappa multiplies it by
-    about 2^5."""
+    tau = kappa s, I = (eps / kappa)(1 - exp(-kappa s)) over the traced affine length s
+    (escaping rays: the medium fills the whole path).  Riding on the geodesic's steps
+    (outside the error norm) the intensity's error is the fifth-order truncation in kappa h:
+    doubling kappa multiplies it by about 2^5.  Under the step control it stays below the
+    tolerance at both opacities (here the geodesic's own steps are short enough)."""
     eps = 0.7
-    errs = {}
-    for kappa in (1e-3, 2e-3):
-        sc = W.scene(emitter="const", freqs=[1.0, 2.0], C_norm=kappa, T0=eps)
-        errs[kappa] = []
-        for alpha, beta in [(1.0, 1.0), (6.0, -2.0), (-14.0, 9.0)]:
-            res = orc.trace_ray(sc, alpha, beta)
-            s = res.s_end
-            assert abs(res.tau_nu[0] - kappa * s) < 1e-13 * kappa * s
-            expect = eps / kappa * (-math.expm1(-kappa * s))
-            errs[kappa].append(abs(res.I_nu[1] - expect) / expect)
-    assert max(errs[1e-3]) < 1e-10
-    ratio = np.array(errs[2e-3]) / np.array(errs[1e-3])
-    assert np.all((ratio > 16) & (ratio < 128)), ratio
+    rays = [(-14.0, 9.0), (10.0, 3.0), (12.0, -8.0)]
+    for mode in ("ride", "controlled"):
+        errs = {}
+        for kappa in (1e-3, 2e-3):
+            sc = W.scene(emitter="const", freqs=[1.0, 2.0], C_norm=kappa, T0=eps,
+                         rt_control=mode)
+            errs[kappa] = []
+            for alpha, beta in rays:
+                res = orc.trace_ray(sc, alpha, beta)
+                assert res.status == 1  # escaped
+                s = res.s_end
+                assert abs(res.tau_nu[0] - kappa * s) < 1e-13 * kappa * s
+                expect = eps / kappa * (-math.expm1(-kappa * s))
+                errs[kappa].append(abs(res.I_nu[1] - expect) / expect)
+        if mode == "ride":
+            assert max(errs[1e-3]) < 1e-10
+            ratio = np.array(errs[2e-3]) / np.array(errs[1e-3])
+            assert np.all((ratio > 16) & (ratio < 128)), ratio
+            ride = errs
+        else:
+            assert max(errs[1e-3] + errs[2e-3]) < 1e-9, errs
+            assert max(errs[2e-3]) <= max(ride[2e-3]), (errs, ride)
+
+
+def test_medium_ends_at_the_stopping_radius(orc):
+    """A captured ray stops at the end of the first step inside r_stop = 1.01 r_+, at a radius
+    that depends on the step sequence; the medium ends at r_stop, so the optical depth of a
+    constant medium is kappa times the affine length to r_stop alone, whatever the
+    tolerance.  That length comes from a separate trace of the geodesic alone (no medium) at
+    rtol 1e-12: its recorded points, linear in r across the last (1e-4 long) step.  The step
+    that crosses r_stop carries a kink of the integrand, resolved by the intensity's step
+    control to the tolerance's level."""
+    kappa, eps = 1e-3, 0.7
+    sc = W.scene(emitter="const", freqs=[1.0], C_norm=kappa, T0=eps)
+    r_stop = 1.01 * orc.horizon(0.9)
+    s_pts, y_pts, _ = orc.trace_path(dict(sc, emitter="none", freqs=[], rtol=1e-12), 1.0, 1.0)
+    inside = np.nonzero(y_pts[:, 0] < r_stop)[0][0]
+    s0, s1 = s_pts[inside - 1], s_pts[inside]
+    r0, r1 = y_pts[inside - 1, 0], y_pts[inside, 0]
+    assert s1 - s0 < 1e-3
+    s_stop = s0 + (r0 - r_stop) / (r0 - r1) * (s1 - s0)
+    tau_stop = kappa * s_stop
+    I_stop = eps / kappa * (-math.expm1(-tau_stop))
+    for rtol in (1e-8, 1e-10):
+        res = orc.trace_ray(dict(sc, rtol=rtol), 1.0, 1.0)
+        assert res.status == 2  # captured
+        assert res.s_end > s_stop  # the last step ends inside r_stop ...
+        assert abs(res.tau_nu[0] - tau_stop) < 1e-8 * tau_stop  # ... the medium does not
+        assert abs(res.I_nu[0] - I_stop) < 1e-8 * I_stop
 
 
 def _torus_sources(a, L, r, th, nu, C):
@@ -290,3 +327,28 @@ def test_torus_radiative_transfer_formal_solution(orc):
             integrand = j / nu0 ** 3 / g * np.exp(-tau)
             I_inv = np.sum(0.5 * (integrand[1:] + integrand[:-1]) * np.diff(s))
             assert abs(nu ** 3 * I_inv - res.I_nu[k]) < 2e-4 * res.I_nu[k]
+
+
+@pytest.mark.parametrize("emitter", ["torus", "synch"])
+def test_intensities_converge_under_the_step_control(orc, emitter):
+    """The transfer equation's intensities are part of the error norm: the image then
+    converges with the tolerance pixel by pixel (rtol 1e-8 against 1e-10 within 2e-6 of
+    each pixel, or of 1e-3 of the image's brightest pixel for dark ones).  Riding on the
+    geodesic's steps instead, the same two tolerances differ by up to ~1e-2 on the torus's
+    shadow and the inner shell, where the emission varies faster than the geodesic."""
+    if emitter == "torus":
+        sc = dict(W.torus_512("fp64"), n_alpha=24, n_beta=24, alpha_min=-8.0, alpha_max=8.0,
+                  beta_min=-8.0, beta_max=8.0)
+    else:
+        sc = W.synch_shell(a=0.0, n=16, precision="fp64")
+    nf = len(sc["freqs"])
+    worst = {}
+    for mode in ("ride", "controlled"):
+        lo = orc.render(dict(sc, rtol=1e-8, rt_control=mode))
+        hi = orc.render(dict(sc, rtol=1e-10, rt_control=mode))
+        assert np.array_equal(lo["status"], hi["status"])
+        Il, Ih = lo["I_nu"][:, :nf], hi["I_nu"][:, :nf]
+        rel = np.abs(Il - Ih) / np.maximum(np.abs(Ih), 1e-3 * np.abs(Ih).max(axis=0))
+        worst[mode] = rel.max()
+    assert worst["controlled"] < 2e-6, worst
+    assert worst["ride"] > 1e-4, worst
