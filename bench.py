@@ -1,12 +1,15 @@
-"""Benchmark: backward ray tracing + radiative transfer of one 512x512 image per step.
+"""Benchmark: backward ray tracing + radiative transfer of one image per step.
 
-Workload: Kerr a = 0.94, r_obs = 1000 M, inclination 30 deg, 512 x 512 pixels over
-[-20, 20]^2 M, analytic thermal torus at nu = 0.5, 1, 2 (the GRRT workload).  One step
-renders the whole image through the C ABI (initial conditions, Cash-Karp integration,
-termination, redshift and transfer).  Metric: ns per photon per Runge-Kutta step
-(= kernel time / attempted steps summed over all rays), plus images/s.
+Workload (default, the largest single-GPU configuration): the 4096x4096 near-edge-on hard
+case, Kerr a = 0.998, r_obs = 1000 M, inclination 85 deg, [-20, 20]^2 M, analytic thermal
+torus at 8 log-spaced frequencies in [0.25, 4], mixed precision (FP32 stages, FP64 initial
+state, checks and compensated sums); its accuracy against the plain FP64 GPU path on the
+same full-size image.  `--workload torus512` times the 512x512 torus (a = 0.94, i = 30 deg,
+nu = 0.5, 1, 2) instead.  One step renders the whole image through the C ABI (initial
+conditions, Cash-Karp integration, termination, redshift and transfer).  Metric: ns per
+photon per Runge-Kutta step (= time / attempted steps summed over all rays), plus images/s.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload hard4096|torus512]
     python bench.py --impl reference ...   # the CPU oracle on the host cores
 
 Under torchrun (N > 1) each rank renders its own image (independent problems, no
@@ -29,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ns per photon per RK step; images/s at <=1e-3 rel image error vs plain FP64 path"
 UNIT = "ns/photon/step"
-WORKLOAD = "torus512"
+DEFAULT_WORKLOAD = "hard4096"
+SCENE_TABLE_BYTES = 640  # the scene-table entry a render copies to the device per scene
 
 
 # Algorithmic flops per attempted Runge-Kutta step, counted from the formulas of the
@@ -40,13 +44,16 @@ FLOPS_GEODESIC_STEP = 895.0       # 6 right-hand sides x 90 (Eqs. 14-15) + stage
 FLOPS_TORUS_STAGE_BASE = 57.0     # flow, redshift, n_e, T_e per stage
 FLOPS_TORUS_STAGE_PER_NU = 19.0   # per frequency per stage
 FLOPS_RT_SUMS_PER_NU = 54.0       # stage and solution sums of tau, I per frequency
+FLOPS_RT_ERROR_PER_NU = 16.0      # the intensity's error estimate (5 weighted terms) and its
+                                  # scaled contribution to the error norm, per frequency
 
 
 def flops_per_step(scene: dict) -> float:
     f = FLOPS_GEODESIC_STEP
     if scene["emitter"] == "torus":
         nf = len(scene["freqs"])
-        f += 6 * (FLOPS_TORUS_STAGE_BASE + FLOPS_TORUS_STAGE_PER_NU * nf) + FLOPS_RT_SUMS_PER_NU * nf
+        f += 6 * (FLOPS_TORUS_STAGE_BASE + FLOPS_TORUS_STAGE_PER_NU * nf) \
+            + (FLOPS_RT_SUMS_PER_NU + FLOPS_RT_ERROR_PER_NU) * nf
     return f
 
 
@@ -60,18 +67,37 @@ def measured_peak(key):
         return None
 
 
+def kernel_source_hash() -> str:
+    """sha256 (16 hex digits) of the CUDA sources the tracing kernels are built from: a DRAM
+    traffic figure measured by ncu is valid only for the binary built from these."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1601_02063_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu*")) + glob.glob(os.path.join(csrc, "*.h"))
+                       + [os.path.join(ROOT, "include", "odyssey.h")]):
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def read_traffic(workload, precision):
-    """DRAM bytes per launch of the tracer from the committed ncu summary (None if the
-    kernel has no capture for this workload)."""
+    """DRAM bytes per launch of the tracer from the committed ncu summary, with the source
+    hash it was measured on: (bytes or None, note).  A figure taken on other sources than the
+    ones built here is stale and is not reported."""
     path = os.path.join(ROOT, "profiles", "trace_traffic.txt")
     if workload is None or not os.path.exists(path):
-        return None
+        return None, "no capture"
+    here = kernel_source_hash()
     for ln in open(path):
         parts = ln.split()
-        if len(parts) >= 3 and not ln.startswith("#") and parts[0] == workload \
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == workload \
                 and parts[1] == precision:
-            return int(parts[2])
-    return None
+            if parts[3] != here:
+                return None, f"stale: captured on sources {parts[3]}, built from {here}"
+            return int(parts[2]), f"ncu capture on sources {here}"
+    return None, "no capture for this workload"
 
 
 def dist_env():
@@ -138,11 +164,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def bench_scene(precision: str, size: int = 512) -> dict:
+WORKLOADS = {
+    "hard4096": "torus 4096x4096, a=0.998, i=85 deg, [-20,20]^2, 8 log-spaced nu in [0.25,4]",
+    "torus512": "torus 512x512, a=0.94, i=30 deg, [-20,20]^2, nu in {0.5,1,2}",
+}
+
+
+def bench_scene(workload: str, precision: str, size: int = 0) -> dict:
     from paper_1601_02063_gb300 import workloads as W
-    sc = W.torus_512(precision=precision)
-    sc.update(n_alpha=size, n_beta=size)
+    sc = W.torus_hard_4096(precision) if workload == "hard4096" else W.torus_512(precision)
+    if size:
+        sc.update(n_alpha=size, n_beta=size)
     return sc
+
+
+def bench_config(args, scene: dict) -> dict:
+    """The `config` of the JSON line (both arms)."""
+    name = args.workload if not args.size else f"{args.workload}@{args.size}"
+    return {"workload": name, "description": WORKLOADS[args.workload],
+            "image": f"{scene['n_alpha']}x{scene['n_beta']}", "a": scene["a"],
+            "inclination_deg": round(math.degrees(scene["theta_obs"]), 6), "r_obs": scene["r_obs"],
+            "window": "[-20,20]^2", "emitter": scene["emitter"], "n_freq": len(scene["freqs"]),
+            "precision": args.precision,
+            "l2": "flushed between timed steps (256 MB write); the image's outputs exceed L2"}
 
 
 def cpu_oracle_sample(scene: dict, target_s: float = 12.0, threads: int = 0):
@@ -220,15 +264,15 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    scene = bench_scene("fp64", args.size)
+    scene = bench_scene(args.workload, "fp64", args.size)
     import oracle
     oracle.build()
     for _ in range(args.warmup):
-        cpu_oracle_sample(scene, target_s=2.0)
+        cpu_oracle_sample(scene, target_s=1.0)
     vals, secs = [], []
     info = None
     for _ in range(args.steps):
-        info = cpu_oracle_sample(scene, target_s=8.0)
+        info = cpu_oracle_sample(scene, target_s=5.0)
         vals.append(info["value"])
         secs.append(info["seconds"])
     value = sum(v * s for v, s in zip(vals, secs)) / sum(secs)
@@ -236,15 +280,34 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": False,
-        "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.size == 512 else f"torus{args.size}",
-                   "image": f"{args.size}x{args.size}", "a": 0.94, "inclination_deg": 30,
-                   "n_freq": 3, "sample": info["sample"]},
+        "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": dict(bench_config(args, scene), precision="fp64"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"],
                          "kind": "oracle", "sample": info["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def image_compare(img, ref, rec, rec_ref, planes: int, n: int) -> dict:
+    """Accuracy of an image against the plain FP64 GPU path on the same scene (device
+    tensors): per frequency the image error sum|I - I_ref| / sum|I_ref|, and per pixel
+    |I - I_ref| / max(|I_ref|, 1e-3 max I_ref) over the pixels of equal ray status (the
+    fraction above 1e-4 and its maximum)."""
+    import torch
+    a = img[:planes * n].view(planes, n)
+    b = ref[:planes * n].view(planes, n)
+    err = ((a - b).abs().sum(dim=1) / b.abs().sum(dim=1)).tolist()
+    st = rec[:n].view(torch.int32)[:, 0]
+    st_ref = rec_ref[:n].view(torch.int32)[:, 0]
+    same = st == st_ref
+    rel = (a - b).abs() / torch.maximum(b.abs(), 1e-3 * b.abs().amax(dim=1, keepdim=True))
+    rel = rel[:, same]
+    return {"image_error": err,
+            "pixels_same_status": float(same.double().mean()),
+            "pixel_frac_above_1e-4": (rel > 1e-4).double().mean(dim=1).tolist(),
+            "pixel_max_rel": rel.amax(dim=1).tolist()}
 
 
 def run_ours(args):
@@ -262,11 +325,12 @@ def run_ours(args):
     from paper_1601_02063_gb300 import shard
 
     cuda_build.build()
-    full_scene = bench_scene(args.precision, args.size)
+    full_scene = bench_scene(args.workload, args.precision, args.size)
     # weak scaling: every rank renders the image; --split: one image in row slabs
     scene = shard.row_shard(full_scene, rank, world) if args.split else full_scene
     tr = B.Tracer(local)
     n = B.n_rays(scene)
+    planes = B.image_planes(scene)
     rec, img = tr.alloc(n, B.n_image(scene))
     stream = torch.cuda.current_stream(local)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB
@@ -305,24 +369,30 @@ def run_ours(args):
     total_ms, steps_all, rays_all = shard.aggregate(total_ms, steps_local, st["rays"], dist)
     value = total_ms * 1e6 / steps_all
     ms_per_step = total_ms / args.steps
+    # the step-count distribution of the image (attempts per ray) and the lane refill
+    rv = rec[:n].view(torch.int32)[:, 1:3].sum(dim=1).double()
+    step_q = torch.quantile(rv[:: max(1, n // (1 << 20))], torch.tensor(
+        [0.5, 0.9, 0.99, 0.999, 1.0], dtype=torch.float64, device=rv.device)).tolist()
 
-    # roofline of the tracing kernel (the only kernel of the step)
+    # roofline of the tracing kernel (the dominant kernel of the step)
     peak = B.odx_fma_peak(tr.ctx, "fp64" if args.precision == "fp64" else "mixed")
     flops = flops_per_step(scene) * steps_local / args.steps  # per launch
     achieved = flops / (kernel_ms * 1e-3)
-    traffic = read_traffic(WORKLOAD if args.size == 512 else None, args.precision)
+    traffic, traffic_note = read_traffic(None if args.size else args.workload, args.precision)
 
-    # the plain FP64 path on the same image: its speed, and the production path's image
-    # error against it (the metric's accuracy condition)
-    fp64_info = None
+    # the plain FP64 path on the same full-size image: its speed, and the production path's
+    # accuracy against it (the metric's accuracy condition), per frequency and per pixel
+    fp64_info, accuracy = None, None
     if args.precision != "fp64":
         sc64 = dict(scene, precision="fp64")
         rec64, img64 = tr.alloc(n, B.n_image(scene))
-        tr.render(sc64, out=(rec64, img64))
-        torch.cuda.synchronize()
+        reps = args.fp64_steps if args.workload == "torus512" else 1
+        if args.workload == "torus512":
+            tr.render(sc64, out=(rec64, img64))
+            torch.cuda.synchronize()
         tr.stats(reset=True)
         t64 = []
-        for _ in range(max(1, args.fp64_steps)):
+        for _ in range(max(1, reps)):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -332,27 +402,20 @@ def run_ours(args):
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
         st64 = tr.stats(reset=True)
-        tr.render(scene, out=(rec, img))
-        torch.cuda.synchronize()
-        nimg = B.n_image(scene)
-        planes = B.image_planes(scene)
-        a = img[:nimg].view(planes, n).double()
-        b = img64[:nimg].view(planes, n).double()
-        errs = ((a - b).abs().sum(dim=1) / b.abs().sum(dim=1)).tolist()
         steps64 = st64["steps_accepted"] + st64["steps_rejected"]
         fp64_info = {"ns_per_photon_step": sum(t64) * 1e6 / steps64,
                      "ms_per_image": statistics.mean(t64),
                      "images_per_s": 1e3 / statistics.mean(t64),
-                     "steps_per_photon": steps64 / st64["rays"]}
-        image_error = errs
+                     "steps_per_photon": steps64 / st64["rays"], "timed_renders": len(t64)}
+        accuracy = image_compare(img, img64, rec, rec64, planes, n)
         del rec64, img64
-    else:
-        image_error = [0.0] * B.image_planes(scene)
+        torch.cuda.empty_cache()
+    image_error = accuracy["image_error"] if accuracy else [0.0] * planes
 
     # secondary: the 64-scene parameter sweep in one persistent launch, autotuned on a
     # small subset, captured as a CUDA graph and replayed
     batched = None
-    if args.sweep and args.size == 512:
+    if args.sweep and not args.size:
         from paper_1601_02063_gb300 import workloads as W
         sweep = W.sweep_64(precision=args.precision)
         saved = B.odx_get_launch(tr.ctx)
@@ -408,7 +471,7 @@ def run_ours(args):
     # secondary: the learned transfer function (trained here on integrator rays) against the
     # mixed and FP64 integrators on the 2048^2 thin-disk image at a = 0.7, i = 45 deg
     surrogate = None
-    if args.surrogate and args.size == 512:
+    if args.surrogate and not args.size:
         from paper_1601_02063_gb300 import workloads as W
         from paper_1601_02063_gb300.surrogate import Surrogate
         sg = Surrogate(tr, max_batch=65536)
@@ -471,14 +534,15 @@ def run_ours(args):
     # inclinations (5..80 deg), 256^2 each, rendered in one batched launch and reduced to
     # F_nu per image and its integral over nu; and the reduction alone on the 512^2 image
     spectra = None
-    if args.precision == "mixed" and args.size == 512 and args.spectra:
+    if args.precision == "mixed" and not args.size and args.spectra:
         incs = [5.0 + 5.0 * k for k in range(16)]
-        lc_scenes = [dict(scene, n_alpha=256, n_beta=256, theta_obs=math.radians(i))
+        lc_base = bench_scene("torus512", "mixed")
+        lc_scenes = [dict(lc_base, n_alpha=256, n_beta=256, theta_obs=math.radians(i))
                      for i in incs]
         n_lc = B.n_rays(lc_scenes)
         rec_lc, img_lc = tr.alloc(n_lc, B.n_image(lc_scenes))
-        planes = B.image_planes(scene)
-        flux_lc = torch.empty(len(lc_scenes) * planes, dtype=torch.float64,
+        lc_planes = B.image_planes(lc_base)
+        flux_lc = torch.empty(len(lc_scenes) * lc_planes, dtype=torch.float64,
                               device=f"cuda:{local}")
         lum_lc = torch.empty(len(lc_scenes), dtype=torch.float64, device=f"cuda:{local}")
 
@@ -587,12 +651,15 @@ def run_ours(args):
             "novikov_thorne": nt_info,
             "workload": "torus, 16 inclinations 5..80 deg, 256x256 each, one batched launch",
             "ms_per_light_curve": ms_lc,
-            "light_curve": [{"inclination_deg": i, "F_nu": flux_lc[planes * k:planes * (k + 1)].tolist(),
+            "light_curve": [{"inclination_deg": i,
+                             "F_nu": flux_lc[lc_planes * k:lc_planes * (k + 1)].tolist(),
                              "F_integrated": float(lum_lc[k])} for k, i in enumerate(incs)],
-            "reduction_512": {"ms": ms_red, "bytes": red_bytes,
-                              "achieved_gbs": red_bytes / ms_red / 1e6, "hbm_peak_gbs": hbm,
-                              "note": "L2 flushed before each call; a 6 MB image is latency-, not "
-                                      "bandwidth-bound"},
+            "reduction": {"image": f"the headline image, {planes} planes of "
+                                   f"{scene['n_alpha']}x{scene['n_beta']}",
+                          "ms": ms_red, "bytes": red_bytes,
+                          "achieved_gbs": red_bytes / ms_red / 1e6, "hbm_peak_gbs": hbm,
+                          "frac": red_bytes / ms_red / 1e6 / hbm if hbm else None,
+                          "bound": "hbm", "note": "L2 flushed before each call"},
         }
         del rec_lc, img_lc
 
@@ -600,7 +667,7 @@ def run_ours(args):
     # a = 0.95, i = 60 deg, FP64) through the FP64 and the mixed path, same metric as the
     # paper's runtime / total steps
     paper_wl = None
-    if args.size == 512 and args.spectra:
+    if not args.size and args.spectra:
         from paper_1601_02063_gb300 import workloads as W
         out_p = {}
         for prec in ("fp64", "mixed"):
@@ -621,43 +688,38 @@ def run_ours(args):
                     "paper_ns_per_photon_step": 16.31, "paper_steps_per_photon": 1505,
                     "paper_hardware": "GeForce GTX 780 Ti, FP64", **out_p}
 
-    # secondary: the 4096^2 near-edge-on hard case (a = 0.998, i = 85 deg, 8 frequencies),
-    # mixed precision, with its step-count distribution; accuracy against FP64 on the same
-    # scene at 512^2
-    hard = None
-    if args.hard and args.size == 512:
-        from paper_1601_02063_gb300 import workloads as W
-        hsc = W.torus_hard_4096(precision="mixed")
-        nh = B.n_rays(hsc)
-        rech, imgh = tr.alloc(nh, B.n_image(hsc))
-        tr.render(hsc, out=(rech, imgh))
+    # secondary: the other torus workload (the 512^2 torus beside the 4096^2 hard case, or the
+    # reverse), mixed precision against the FP64 path on the same full-size image
+    other = None
+    if args.other and not args.size:
+        oname = "torus512" if args.workload == "hard4096" else "hard4096"
+        osc = bench_scene(oname, "mixed")
+        no, po = B.n_rays(osc), B.image_planes(osc)
+        reco, imgo = tr.alloc(no, B.n_image(osc))
+        tr.render(osc, out=(reco, imgo))
         torch.cuda.synchronize()
         tr.stats(reset=True)
-        ms_h = timed(lambda: tr.render(hsc, out=(rech, imgh)), 1)
-        sth = tr.stats(reset=True)
-        rv = rech[:nh].view(torch.int32)[:, 1:3].sum(dim=1).double()
-        qs = torch.quantile(rv[:: max(1, nh // (1 << 20))], torch.tensor(
-            [0.5, 0.9, 0.99, 0.999], dtype=torch.float64, device=rv.device)).tolist()
-        del rech, imgh
-        small = dict(hsc, n_alpha=512, n_beta=512)
-        recs, imgs = tr.alloc(512 * 512, B.n_image(small))
-        tr.render(dict(small, precision="fp64"), out=(recs, imgs))
-        torch.cuda.synchronize()
-        ref = imgs[:B.n_image(small)].view(8, -1).clone()
-        tr.render(small, out=(recs, imgs))
-        torch.cuda.synchronize()
-        got = imgs[:B.n_image(small)].view(8, -1)
-        errs = ((got - ref).abs().sum(dim=1) / ref.abs().sum(dim=1)).tolist()
-        steps_h = sth["steps_accepted"] + sth["steps_rejected"]
-        hard = {"workload": "torus 4096x4096, a=0.998, i=85 deg, 8 log-spaced nu in [0.25,4]",
-                "precision": "mixed", "ms_per_image": ms_h, "images_per_s": 1e3 / ms_h,
-                "ns_per_photon_step": ms_h * 1e6 / steps_h, "steps_per_photon": steps_h / nh,
-                "steps_per_photon_quantiles_50_90_99_999": qs,
-                "lane_refill_efficiency": sth["lane_active"] / max(1, sth["lane_slots"]),
-                "image_error_vs_fp64_at_512": errs}
+        reps = 5 if oname == "torus512" else 2
+        ms_o = timed(lambda: tr.render(osc, out=(reco, imgo)), reps)
+        sto = tr.stats(reset=True)
+        steps_o = (sto["steps_accepted"] + sto["steps_rejected"]) / reps
+        rec64, img64 = tr.alloc(no, B.n_image(osc))
+        tr.stats(reset=True)
+        ms_o64 = timed(lambda: tr.render(dict(osc, precision="fp64"), out=(rec64, img64)), 1)
+        sto64 = tr.stats(reset=True)
+        steps_o64 = sto64["steps_accepted"] + sto64["steps_rejected"]
+        other = {"workload": oname, "description": WORKLOADS[oname], "precision": "mixed",
+                 "ms_per_image": ms_o, "images_per_s": 1e3 / ms_o,
+                 "ns_per_photon_step": ms_o * 1e6 / steps_o, "steps_per_photon": steps_o / no,
+                 "lane_refill_efficiency": sto["lane_active"] / max(1, sto["lane_slots"]),
+                 "accuracy_vs_fp64": image_compare(imgo, img64, reco, rec64, po, no),
+                 "fp64_path": {"ms_per_image": ms_o64, "images_per_s": 1e3 / ms_o64,
+                               "ns_per_photon_step": ms_o64 * 1e6 / steps_o64,
+                               "steps_per_photon": steps_o64 / no}}
         if world == 1 and not args.skip_cpu:
-            hard["cpu_oracle"] = cpu_oracle_pixels([hsc], 4096, W.SEED + 400)
-        del recs, imgs, ref
+            other["cpu_oracle"] = cpu_oracle_pixels([osc], 4096, 20160109 + 400)
+        del reco, imgo, rec64, img64
+        torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     rec_h = torch.empty(n * B.RECORD_BYTES // 8, dtype=torch.float64).pin_memory().numpy()
@@ -691,32 +753,32 @@ def run_ours(args):
         "scaling": "strong" if (args.split and world > 1) else "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.size == 512 else f"torus{args.size}",
-                   "image": f"{args.size}x{args.size}", "a": 0.94, "inclination_deg": 30,
-                   "r_obs": 1000, "window": "[-20,20]^2", "emitter": "torus", "n_freq": 3,
-                   "precision": args.precision, "l2": "flushed between timed steps (256 MB)",
-                   "launch": B.odx_get_launch(tr.ctx)},
+        "config": dict(bench_config(args, full_scene), launch=B.odx_get_launch(tr.ctx)),
         "images_per_s": 1e3 / ms_per_step * world,
         "steps_per_photon": steps_all / rays_all,
         "image_error_vs_fp64": image_error,
+        "accuracy_vs_fp64": accuracy,
         "fp64_path": fp64_info,
+        "steps_per_photon_quantiles_50_90_99_999_max": step_q,
         "fp64_step_fraction": st["steps_fp64"] / max(1, steps_local),
         "lane_refill_efficiency": st["lane_active"] / max(1, st["lane_slots"]),
         "batched": batched,
         "surrogate": surrogate,
-        "hard_case": hard,
+        "other_workload": other,
         "spectra": spectra,
         "paper_workload": paper_wl,
         "gpu_launches": args.steps * (3 if args.precision == "mixed" else 1),
         "tracer_kernel_ms": kernel_ms,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": traffic_note,
+                     "flops_per_step": flops_per_step(scene),
                      "peak_source": "measured FMA-chain microbenchmark, same run",
                      "kernel": "trace_mixed_kernel" if args.precision == "mixed"
                                else "trace_fp64_kernel",
                      "pipe": "fp64" if args.precision == "fp64" else "fp32"},
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": 304,
+                "h2d_bytes_per_step": SCENE_TABLE_BYTES,
                 "d2h_bytes_per_step": n * B.RECORD_BYTES + 8 * B.n_image(scene)},
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -738,8 +800,9 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="timed renders of the plain FP64 path beside the production path")
-    ap.add_argument("--size", type=int, default=512,
-                    help="image side (the workload is 512; smaller sizes are for profiling)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--size", type=int, default=0,
+                    help="image side override (profiling of smaller cases; 0: the workload's)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
     ap.add_argument("--split", action="store_true",
                     help="N > 1: split one image into row slabs (strong scaling) instead of "
@@ -748,8 +811,8 @@ def main():
                     help="omit the 64-scene batched sweep measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="omit training and timing the learned surrogate")
-    ap.add_argument("--no-hard", dest="hard", action="store_false",
-                    help="omit the 4096^2 near-edge-on hard case")
+    ap.add_argument("--no-other", dest="other", action="store_false",
+                    help="omit the other torus workload (512^2 torus / 4096^2 hard case)")
     ap.add_argument("--no-spectra", dest="spectra", action="store_false",
                     help="omit the spectra, light curves and the paper's timing workload")
     args = ap.parse_args()

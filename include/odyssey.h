@@ -83,6 +83,19 @@ extern "C" {
 #define ODX_FP64 0  /* every stage in FP64                                             */
 #define ODX_MIXED 1 /* FP32 stages in bulk, FP64 within r_switch, compensated sums     */
 
+/* step control of the transfer equation (Section 2.3, Eqs. 30-31, integrated along with the
+ * geodesic; the paper names no error norm for them).  In both modes the medium ends at the
+ * stopping radius horizon_factor * r_+: no emission or absorption inside it, so a captured
+ * ray's intensity does not depend on where its last step lands. */
+#define ODX_RT_CONTROLLED 0 /* each invariant intensity I_k enters the Cash-Karp error norm
+                               with the scale |I_k| + |h dI_k/ds| + 3e-5 B_nu(T0)/nu^3 (the
+                               medium's source function at its temperature scale T0, seen
+                               at nu_k); tau stays out (its error reaches I through
+                               exp(-tau)).  Default.                                       */
+#define ODX_RT_RIDE 1       /* only the geodesic components set the steps; tau and I ride
+                               on them (intensities good to ~1e-3 - 1e-2 per pixel where
+                               the emission varies faster than the geodesic)               */
+
 /* direction reading of the traced photon */
 #define ODX_CONV_PHYSICAL 0 /* the real outgoing photon traced back in affine time (default) */
 #define ODX_CONV_LITERAL 1  /* Eqs. 24-26 taken as the velocity of the traced photon        */
@@ -113,7 +126,7 @@ typedef struct odx_scene {
     int32_t max_steps;              /* cap on Runge-Kutta attempts per ray (>= 1)       */
     int32_t convention;             /* ODX_CONV_*                                        */
     int32_t precision;              /* ODX_FP64 or ODX_MIXED                             */
-    int32_t reserved;               /* must be 0                                         */
+    int32_t rt_control;             /* ODX_RT_*: step control of the transfer equation   */
     double rtol_fp32;               /* ODX_MIXED: relative tolerance of the FP32 stages  */
     double r_switch;                /* ODX_MIXED: FP64 stages where r < r_switch         */
     double n_e0;                    /* synchrotron shell: n_e at r = 1 (cm^-3), > 0      */
@@ -334,6 +347,13 @@ int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Ad
  * unwritten and raises a device flag, reported (and cleared) as ODX_ERR_DEVICE_FLAG by the
  * next odx_mlp_get_params, odx_mlp_gradients or odx_surrogate_render call. */
 int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
+/* Test hook for the tensor-core kernels' failure path: the number of polls after which a
+ * wait inside the tile loop of the forward and backward chains (odx_mlp_forward,
+ * odx_mlp_train_step, odx_mlp_gradients) gives up; 0 restores the default, 2^20 polls.  A
+ * kernel that gives up raises the device flag and returns after waiting, with the default
+ * limit, for its own copies and MMAs in flight and freeing its tensor memory; the flag is
+ * reported as above.  No counterpart in the paper. */
+int32_t odx_mlp_set_wait_limit(odx_mlp *mlp, uint32_t tries);
 /* Training rows: x_dev[n][4] = (alpha / 20, beta / 20, a, cos i), 16-byte aligned;
  * t_dev[n][8] as written by odx_mlp_targets (captured flag, log r_cross, phi_cross / pi, g,
  * crossing mask, g mask, 0, 0), 16-byte aligned.  Both device pointers, caller-owned.
@@ -375,14 +395,16 @@ int32_t odx_surrogate_render(odx_mlp *mlp, const odx_scene *scene_host, double b
  * is a deployment variant of odx_render.
  *
  * The ray queue counter, the device statistics and the scene table live in one file-scope
- * device array of 36,864 bytes that every GPU loading this library holds until the process
+ * device array of 45,056 bytes that every GPU loading this library holds until the process
  * exits; at most ODX_STATIC_MAX_SCENES scenes per call (more: ODX_ERR_TOO_LARGE, nothing
  * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
  * as odx_render) and the scene descriptions in host memory.  The call works on the calling
  * thread's current device.  Its first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture.  The call allocates no device memory and frees none, and copies the scene table
- * into the array with a stream-ordered copy.
+ * into the array with a stream-ordered copy from a buffer on its own stack; while `stream`
+ * is capturing a graph it returns ODX_ERR_UNSUPPORTED and does nothing (a replay would
+ * copy from that stack frame after the call has returned).
  *
  * Every call shares the one array, which keeps the previous call's contents (the counter is
  * cleared on each call): calls whose work overlaps on the GPU (on different streams, or

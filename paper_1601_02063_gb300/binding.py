@@ -23,6 +23,7 @@ RUNNING, ESCAPED, CAPTURED, DISK_HIT, MAXSTEPS, NUMERR = range(6)
 EMITTERS = {"none": 0, "thin_disk": 1, "torus": 2, "nt_disk": 3, "synch": 4, "spot": 5}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 CONVENTIONS = {"physical": 0, "literal": 1}
+RT_CONTROL = {"controlled": 0, "ride": 1}
 
 
 class odx_scene(C.Structure):
@@ -40,7 +41,7 @@ class odx_scene(C.Structure):
         ("rtol", C.c_double), ("h0", C.c_double), ("hmax_frac", C.c_double),
         ("horizon_factor", C.c_double),
         ("max_steps", C.c_int32), ("convention", C.c_int32),
-        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("precision", C.c_int32), ("rt_control", C.c_int32),
         ("rtol_fp32", C.c_double), ("r_switch", C.c_double),
         ("n_e0", C.c_double), ("beta_B", C.c_double), ("mass", C.c_double),
         ("spot_r", C.c_double), ("spot_size", C.c_double), ("spot_phase", C.c_double),
@@ -112,6 +113,7 @@ _SIGNATURES = [
     ("odx_mlp_get_params", C.c_int32, [_P, _P]),
     ("odx_mlp_set_params", C.c_int32, [_P, _P]),
     ("odx_mlp_forward", C.c_int32, [_P, _P, C.c_int64, _P, _P]),
+    ("odx_mlp_set_wait_limit", C.c_int32, [_P, C.c_uint32]),
     ("odx_mlp_gradients", C.c_int32, [_P, _P, _P, C.c_int64, _P, _P]),
     ("odx_mlp_train_step", C.c_int32, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
     ("odx_mlp_targets", C.c_int32, [_P, _P, _P, C.c_int64, C.c_double, _P, _P, _P]),
@@ -310,6 +312,10 @@ def odx_mlp_set_params(mlp, params: np.ndarray) -> None:
     _ok(lib().odx_mlp_set_params(mlp, p.ctypes.data), "odx_mlp_set_params")
 
 
+def odx_mlp_set_wait_limit(mlp, tries: int) -> None:
+    _ok(lib().odx_mlp_set_wait_limit(mlp, int(tries)), "odx_mlp_set_wait_limit")
+
+
 def odx_mlp_forward(mlp, x_ptr: int, n: int, y_ptr: int, stream: int | None = None) -> None:
     _ok(lib().odx_mlp_forward(mlp, x_ptr, n, y_ptr, stream or None), "odx_mlp_forward")
 
@@ -365,7 +371,7 @@ def scene_struct(d: dict) -> odx_scene:
     s.max_steps = int(d["max_steps"])
     s.convention = CONVENTIONS[d.get("convention", "physical")]
     s.precision = PRECISIONS[d.get("precision", "fp64")]
-    s.reserved = 0
+    s.rt_control = RT_CONTROL[d.get("rt_control", "controlled")]
     cn = d.get("C_norm")
     if cn is None:
         cn = odx_torus_norm(d["a"], d.get("nu_norm", 1.0), d["ne_index"], d["T0"],

@@ -252,6 +252,26 @@ __host__ __device__ inline SynchK synch_constants(const odx_scene &s)
     return k;
 }
 
+// ---- step control of the transfer equation (Section 2.3) ----------------------------------
+// The invariant intensities I_k enter the Cash-Karp error norm with the scale
+// |I_k| + |h dI_k/ds| + rt_floor(s, nu_k): the floor is kRtFloorFrac times the medium's
+// source function at its temperature scale T0 seen at nu, B_nu(T0) / nu^3, in the units the
+// stages carry (torus: 2 / (exp(nu / T0) - 1); synchrotron shell: the CGS value
+// (2 h / c^2) / (exp(h nu / (T0 m_e c^2)) - 1) divided by Aj, nu in Hz), so that emission far
+// below the medium's own intensity scale does not set the step.  ODX_RT_RIDE: infinite (the
+// intensities stay out of the norm).
+constexpr double kRtFloorFrac = 3e-5;
+__host__ __device__ inline double rt_floor(const odx_scene &s, double nu)
+{
+    if (s.rt_control == ODX_RT_RIDE) return INFINITY;
+    if (s.emitter == ODX_EMIT_SYNCH) {
+        const double kT = s.T0 * kCgsMe * kCgsC * kCgsC;
+        const double src = 2.0 * kCgsH / (kCgsC * kCgsC) / expm1(kCgsH * nu / kT);
+        return kRtFloorFrac * src / synch_constants(s).Aj;
+    }
+    return kRtFloorFrac * 2.0 / expm1(nu / s.T0);
+}
+
 // ---- Keplerian hot spot (Section 4.4): the centre's circular equatorial orbit --------------
 __host__ __device__ inline double spot_orbit_radius(const odx_scene &s)
 {

@@ -81,6 +81,7 @@ struct odx_mlp {
     bf16 *wpackB = nullptr;  // ... and as backward operands (W)
     float *dw_part = nullptr;  // per-split weight-gradient partial sums
     int *tc_err = nullptr;  // set by a tensor-core kernel whose wait timed out
+    uint32_t wait_limit = 0;  // polls of an in-loop tensor-core wait (0: TC_WAIT)
     int num_sms = 0;
     // surrogate render workspace
     int64_t surr_cap = 0;
@@ -350,6 +351,7 @@ struct TcArgs {
     const bf16 *dZ4;    // TC_BWD: input
     bf16 *dZ[5];        // TC_BWD: dZ_3, dZ_2, dZ_1 written
     int *err;
+    uint32_t wait_limit;  // polls of a wait inside the tile loop (teardown waits use TC_WAIT)
 };
 
 // Forward operands: B[n][k] = W_l[k][n] (z = h W); backward operands: B[k][n] = W_l[k][n]
@@ -526,7 +528,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
             // A tile written and previous accumulator reads done; weights present
             bool to = false;
             if (tid == 0 && w_pending) {
-                to = !tc::mbar_wait(wbar, wphase, TC_WAIT);
+                to = !tc::mbar_wait(wbar, wphase, A.wait_limit);
                 if (!to) {
                     wphase ^= 1u;
                     w_pending = false;
@@ -551,7 +553,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
             // accumulator complete: A and B free again (thread 0 polls, the rest sleep in the
             // block barrier instead of spinning on the mbarrier)
             if (tid == 0) {
-                to = !tc::mbar_wait(mbar, mphase, TC_WAIT);
+                to = !tc::mbar_wait(mbar, mphase, A.wait_limit);
                 if (!to) {
                     mphase ^= 1u;
                     m_pending = false;
@@ -994,9 +996,14 @@ __global__ void __launch_bounds__(DW_THREADS, 1) mlp_dw_tc(const __grid_constant
         pending = to;
     }
     if (__syncthreads_or(to) || failed) {
-        if (tid == 0) atomicExch(A.err, 1);
+        if (tid == 0) {
+            atomicExch(A.err, 1);
+            if (pending) tc::mbar_wait(mbar[last_st], (mph >> last_st) & 1u, TC_WAIT);  // bounded
+        }
         failed = true;
     }
+    tc::fence_before_sync();
+    __syncthreads();
     tc::fence_after_sync();
     if (!failed) {
         // rows k = 128 (warp / 4) + 32 (warp % 4) + lane of the partial, 256 columns
@@ -1052,6 +1059,7 @@ TcArgs chain_args(odx_mlp *m, const bf16 *wpack, int64_t n)
     a.wpack = wpack;
     a.n_rows = n;
     a.err = m->tc_err;
+    a.wait_limit = m->wait_limit ? m->wait_limit : TC_WAIT;
     for (int l = 1; l <= 4; ++l) {
         a.Z[l] = m->Z[l];
         a.H[l] = m->H[l];
@@ -1241,6 +1249,13 @@ int32_t odx_mlp_set_params(odx_mlp *m, const float *host)
     MLP_CUDA(cudaMemset(m->m2, 0, NPARAM * sizeof(float)));
     m->step = 0;
     MLP_CUDA(cudaDeviceSynchronize());
+    return ODX_OK;
+}
+
+int32_t odx_mlp_set_wait_limit(odx_mlp *m, uint32_t tries)
+{
+    if (!m) return ODX_ERR_INVALID_ARG;
+    m->wait_limit = tries;
     return ODX_OK;
 }
 

@@ -133,7 +133,8 @@ int32_t validate_scene(odx_ctx *ctx, const odx_scene &s, int k, bool list_mode)
     if (s.precision == ODX_MIXED &&
         (!(s.rtol_fp32 > 0.0) || !finite(s.rtol_fp32) || !finite(s.r_switch) || s.r_switch < 0.0))
         return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: bad mixed-precision controls", k);
-    if (s.reserved != 0) return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: reserved must be 0", k);
+    if (s.rt_control != ODX_RT_CONTROLLED && s.rt_control != ODX_RT_RIDE)
+        return fail(ctx, ODX_ERR_INVALID_ARG, "scene %d: unknown rt_control", k);
     return ODX_OK;
 }
 
@@ -364,10 +365,14 @@ void fill_dev_scene(DevScene &d, const odx_scene &s, int64_t ray_begin, int64_t 
         const double nu = nf > 0 ? s.freqs[k < nf ? k : nf - 1] * nu_scale : 1.0;
         d.f_nu[k] = (float)nu;
         d.f_inv_nu3[k] = (nu > 0.0) ? (float)(1.0 / (nu * nu * nu)) : 0.f;
+        d.rt_floor[k] = (nf > 0 && (s.emitter == ODX_EMIT_TORUS || synch))
+                            ? rt_floor(s, s.freqs[k < nf ? k : nf - 1])
+                            : INFINITY;
+        d.f_rt_floor[k] = (float)d.rt_floor[k];
     }
 }
 
-static_assert(sizeof(MedConst) == (11 + 2 * ODX_MAX_FREQ) * 4, "MedConst has no padding");
+static_assert(sizeof(MedConst) == (11 + 3 * ODX_MAX_FREQ) * 4, "MedConst has no padding");
 
 static MedConst medium_const(const DevScene &d)
 {
@@ -380,6 +385,7 @@ static MedConst medium_const(const DevScene &d)
     for (int k = 0; k < ODX_MAX_FREQ; ++k) {
         m.nu[k] = d.f_nu[k];
         m.inv_nu3[k] = d.f_inv_nu3[k];
+        m.rt_floor[k] = d.f_rt_floor[k];
     }
     m.inv_kc = d.f_inv_kc;
     m.ky = d.f_ky;

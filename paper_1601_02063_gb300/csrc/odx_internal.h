@@ -35,6 +35,9 @@ struct DevScene {
     // FP64 constants of the initial state (Section 2.2) shared by the scene's pixels:
     // sin, cos of theta_obs and phi_obs, sqrt(r_obs^2 + a^2), r_ISCO and the stop radius
     double o_sto, o_cto, o_spo, o_cpo, o_Ro, o_r_isco, o_r_stop;
+    // error-scale floors of the transfer intensities (rt_floor, kerr_device.cuh), per
+    // frequency slot, padded past n_freq with the last; infinite without transfer
+    double rt_floor[ODX_MAX_FREQ];
     // FP32 constants of the FP32 stages (filled by fill_dev_scene)
     float f_r_out, f_hmax_frac, f_rtol32;
     float f_T_index;   // 1/T_e = exp(T_index ln r) / T0
@@ -49,6 +52,7 @@ struct DevScene {
     // 1 / Theta_e from f_T_index, f_inv_T0 as for the torus; SynchK in FP32
     float f_inv_kc, f_ky, f_Atau;
     int32_t f_synch;
+    float f_rt_floor[ODX_MAX_FREQ];  // rt_floor in FP32
     // hot spot: sqrt(r_s^2 + a^2), Omega, the centre's azimuth at emission time 0 for an
     // image at t_obs (spot_phase + Omega t_obs, reduced mod 2 pi), 4 r_spot
     float f_spot_Rs, f_spot_om, f_spot_ph, f_spot_R4;
@@ -69,7 +73,7 @@ struct DevStats {
 // parameters when every ray of a launch shares one medium.
 struct MedConst {
     float T_index, inv_T0, lr_pref, c2_pref, pref0;
-    float nu[ODX_MAX_FREQ], inv_nu3[ODX_MAX_FREQ];
+    float nu[ODX_MAX_FREQ], inv_nu3[ODX_MAX_FREQ], rt_floor[ODX_MAX_FREQ];
     float inv_kc, ky, Atau, r_out;
     int32_t synch;
     int32_t spot;  // the launch's scenes are hot spots

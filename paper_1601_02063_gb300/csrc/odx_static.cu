@@ -30,7 +30,7 @@ using odx::DevStats;
 constexpr size_t kQueueOffset = 0;
 constexpr size_t kStatsOffset = 64;
 constexpr size_t kScenesOffset = 256;
-constexpr size_t kStaticBytes = 36864;
+constexpr size_t kStaticBytes = 45056;
 static_assert(kScenesOffset + ODX_STATIC_MAX_SCENES * sizeof(DevScene) <= kStaticBytes,
               "scene table does not fit the static scratch");
 static_assert(sizeof(DevStats) <= kScenesOffset - kStatsOffset, "stats do not fit");
@@ -100,6 +100,11 @@ extern "C" int32_t odx_render_static(const odx_scene *scenes, int32_t n_scenes,
     if (src != ODX_OK) return src;
 
     cudaStream_t st = (cudaStream_t)stream;
+    // the scene table below is copied from this call's stack frame: a graph captured from
+    // the call would replay a copy from memory that no longer holds it
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &capture) != cudaSuccess) return ODX_ERR_CUDA;
+    if (capture != cudaStreamCaptureStatusNone) return ODX_ERR_UNSUPPORTED;
     unsigned char *base = setup.scratch;
     // pageable source: the copy has taken the table before cudaMemcpyAsync returns
     if (cudaMemcpyAsync(base + kScenesOffset, table, n_scenes * sizeof(DevScene),

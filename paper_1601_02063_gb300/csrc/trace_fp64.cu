@@ -12,9 +12,11 @@
 // indices are handed out by rank within the ballot (with the warp-coherent queue only once
 // the whole warp is done).
 //
-// Radiative transfer (Section 2.3, Eqs. 30-31) rides on the same stages as extra
+// Radiative transfer (Section 2.3, Eqs. 30-31) runs on the same stages as extra
 // components: the optical depth tau_k needs its stage values (dI/ds depends on exp(-tau)),
-// the invariant intensity only its weighted sum, so only tau keeps per-stage slopes.
+// the invariant intensity only its weighted sums (the fifth-order increment and the error
+// estimate), so only tau keeps per-stage slopes.  The intensities are under the step
+// control (ODX_RT_CONTROLLED) and the medium ends at the stopping radius.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             R.n_acc = R.n_rej = R.n_cross = 0;
 #pragma unroll
             for (int k = 0; k < NF + 1; ++k) R.tau[k] = R.I[k] = 0.0;
-            if constexpr (NF > 0) load_medium_t<double>(S, r_isco, m);
+            if constexpr (NF > 0) load_medium_t<double>(S, r_isco, R.r_stop, m);
             const Geo<double> g{R.a, R.L, R.sgn};
             derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
             R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);
@@ -183,9 +185,9 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             // ---- one Cash-Karp attempt ----------------------------------------------------------
             const DevScene &S = A.scenes[R.scene];
             const Geo<double> g{R.a, R.L, R.sgn};
-            double y5[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1];
+            double y5[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1], eI[NF + 1];
             const double h = R.h;
-            ck_attempt<double, NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, dy, e, dtau, dI);
+            ck_attempt<double, NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, dy, e, dtau, dI, eI);
 #pragma unroll
             for (int i = 0; i < 6; ++i) y5[i] = R.y[i] + dy[i];
             double errmax = 0.0;
@@ -194,6 +196,14 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             for (int i = 0; i < 6; ++i) {
                 const double sc = fabs(R.y[i]) + fabs(R.hs * R.k1[i]) + 1e-30;
                 const double v = fabs(e[i] / sc);
+                nan_err |= isnan(v);
+                errmax = fmax(errmax, v);
+            }
+            // the intensities under the step control (ODX_RT_RIDE: infinite floors)
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                const double sc = fabs(R.I[k]) + fabs(R.hs * R.kI1[k]) + m.I_floor[k];
+                const double v = fabs(eI[k] / sc);
                 nan_err |= isnan(v);
                 errmax = fmax(errmax, v);
             }
@@ -221,10 +231,13 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                     }
                 }
                 // hot spot: d_spot is the distance from the spot's centre at y5, the step's
-                // end.  It stays infinite where the lower bound d >= |sqrt(r^2 + a^2) - R_s|
-                // (two points at those cylindrical radii are at least that far apart) keeps
-                // y5 outside the spot and the step cap from binding: there the exact
-                // distance changes nothing and its three FP64 sincos are skipped.
+                // end.  It stays infinite where the lower bound d >= |rho - R_s| keeps y5
+                // outside the spot and the step cap from binding: there the exact distance
+                // changes nothing and its three FP64 sincos are skipped.  In the spot's
+                // pseudo-Cartesian coordinates x, y = sqrt(r^2 + a^2) (cos, sin) phi (no
+                // sin theta), z = r cos theta, a point lies at rho = sqrt(r^2 + a^2) from the
+                // z axis and the centre (z = 0) at R_s, so d^2 = (horizontal separation)^2
+                // + z^2 >= (rho - R_s)^2 by the triangle inequality in the x-y plane.
                 double d_spot = INFINITY;
                 bool near_spot = false;
                 if (status == ODX_RUNNING && S.s.emitter == ODX_EMIT_SPOT) {

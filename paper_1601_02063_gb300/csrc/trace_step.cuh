@@ -54,14 +54,20 @@ template <typename T>
 struct MediumT {
     T ne_index, inv_2w2, T0, inv_T0, T_index, C_norm, r_isco;
     T freqs[ODX_MAX_FREQ];
+    T I_floor[ODX_MAX_FREQ];  // error-scale floors of the intensities (rt_floor)
+    T r_stop;                 // the medium ends inside the stopping radius
     int n_freq;
     int synch;
     T inv_kc, ky, Atau, r_out;
 };
 
 template <typename T>
-__device__ __forceinline__ void load_medium_t(const DevScene &S, double r_isco, MediumT<T> &m)
+__device__ __forceinline__ void load_medium_t(const DevScene &S, double r_isco, double r_stop,
+                                              MediumT<T> &m)
 {
+    m.r_stop = (T)r_stop;
+#pragma unroll
+    for (int k = 0; k < ODX_MAX_FREQ; ++k) m.I_floor[k] = (T)S.rt_floor[k];
     m.ne_index = (T)S.s.ne_index;
     m.inv_2w2 = (T)(1.0 / (2.0 * S.s.theta_width * S.s.theta_width));
     m.T0 = (T)S.s.T0;
@@ -181,6 +187,12 @@ __device__ __forceinline__ void derivs(const Geo<T> &g, const MediumT<T> &m, con
                         F * (rm1 * iSD + r * iS * iS));
         f[5] = g.sgn * (s * c * iS * (L * L * is2 * is2 - a2) - a2 * s * c * F * iS * iS);
 
+        // the medium ends at the stopping radius (rays stop inside it)
+        if (r < m.r_stop) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) ftau[k] = fI[k] = T(0);
+            return;
+        }
         // torus: Keplerian flow where r >= r_ISCO and timelike, else ZAMO; g from Eq. 2
         const T A = rr * rr - a2 * Del * s2;
         const T gtt = -(T(1) - twor * iS);
@@ -268,19 +280,24 @@ __device__ __forceinline__ void derivs_stage(const Geo<T> &g, const MediumT<T> &
 }
 
 // One Cash-Karp attempt of size h from (y, tau) with first stage (k1, kt1, kI1).
-// Returns the fifth-order increments dy (y5 = y + dy), the embedded error estimate e of the
-// geodesic components, and the fifth-order increments dtau, dI of the transfer components.
-// tau needs its stage values (dI/ds depends on exp(-tau)); I only its weighted sum.
+// Returns the fifth-order increments dy (y5 = y + dy), the embedded error estimates e of the
+// geodesic components and eI of the intensities, and the fifth-order increments dtau, dI of
+// the transfer components.  tau needs its stage values (dI/ds depends on exp(-tau)); I only
+// its weighted sums.
 template <typename T, int NF>
 __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m, const T y[6],
                                            const T k1[6], const T *tau, const T *kt1,
-                                           const T *kI1, T h, T dy[6], T e[6], T *dtau, T *dI)
+                                           const T *kI1, T h, T dy[6], T e[6], T *dtau, T *dI,
+                                           T *eI)
 {
     constexpr int N = NF + 1;
     T k2[6], k3[6], k4[6], k5[6], k6[6], yt[6];
-    T t2[N], t3[N], t4[N], t5[N], t6[N], tt[N], fI[N], sI[N];
+    T t2[N], t3[N], t4[N], t5[N], t6[N], tt[N], fI[N], sI[N], sE[N];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] = T(CK_B1) * kI1[k];
+    for (int k = 0; k < NF; ++k) {
+        sI[k] = T(CK_B1) * kI1[k];
+        sE[k] = T(CK_E1) * kI1[k];
+    }
 
 #pragma unroll
     for (int i = 0; i < 6; ++i) yt[i] = y[i] + h * (T(CK_A21) * k1[i]);
@@ -294,7 +311,10 @@ __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m,
     for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * (T(CK_A31) * kt1[k] + T(CK_A32) * t2[k]);
     derivs_stage<T, NF>(g, m, yt, tt, k3, t3, fI);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B3) * fI[k];
+    for (int k = 0; k < NF; ++k) {
+        sI[k] += T(CK_B3) * fI[k];
+        sE[k] += T(CK_E3) * fI[k];
+    }
 
 #pragma unroll
     for (int i = 0; i < 6; ++i)
@@ -304,7 +324,10 @@ __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m,
         tt[k] = tau[k] + h * (T(CK_A41) * kt1[k] + T(CK_A42) * t2[k] + T(CK_A43) * t3[k]);
     derivs_stage<T, NF>(g, m, yt, tt, k4, t4, fI);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B4) * fI[k];
+    for (int k = 0; k < NF; ++k) {
+        sI[k] += T(CK_B4) * fI[k];
+        sE[k] += T(CK_E4) * fI[k];
+    }
 
 #pragma unroll
     for (int i = 0; i < 6; ++i)
@@ -315,6 +338,8 @@ __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m,
         tt[k] = tau[k] + h * (T(CK_A51) * kt1[k] + T(CK_A52) * t2[k] + T(CK_A53) * t3[k] +
                               T(CK_A54) * t4[k]);
     derivs_stage<T, NF>(g, m, yt, tt, k5, t5, fI);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) sE[k] += T(CK_E5) * fI[k];  // b5 of stage 5 is 0
 
 #pragma unroll
     for (int i = 0; i < 6; ++i)
@@ -326,7 +351,10 @@ __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m,
                               T(CK_A64) * t4[k] + T(CK_A65) * t5[k]);
     derivs_stage<T, NF>(g, m, yt, tt, k6, t6, fI);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) sI[k] += T(CK_B6) * fI[k];
+    for (int k = 0; k < NF; ++k) {
+        sI[k] += T(CK_B6) * fI[k];
+        sE[k] += T(CK_E6) * fI[k];
+    }
 
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
@@ -338,6 +366,7 @@ __device__ __forceinline__ void ck_attempt(const Geo<T> &g, const MediumT<T> &m,
     for (int k = 0; k < NF; ++k) {
         dtau[k] = h * (T(CK_B1) * kt1[k] + T(CK_B3) * t3[k] + T(CK_B4) * t4[k] + T(CK_B6) * t6[k]);
         dI[k] = h * sI[k];
+        eI[k] = h * sE[k];
     }
 }
 
@@ -347,8 +376,8 @@ __device__ __noinline__ void ck_geo_increment(const Geo<T> &g, const T y[6], con
                                               T dy[6])
 {
     const MediumT<T> m{};
-    T e[6], z[1] = {T(0)}, d1[1], d2[1];
-    ck_attempt<T, 0>(g, m, y, k1, z, z, z, h, dy, e, d1, d2);
+    T e[6], z[1] = {T(0)}, d1[1], d2[1], d3[1];
+    ck_attempt<T, 0>(g, m, y, k1, z, z, z, h, dy, e, d1, d2, d3);
 }
 
 // First entry into the hot spot inside an accepted step: bisection on the size of a single

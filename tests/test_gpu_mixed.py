@@ -3,14 +3,16 @@ optional FP64 region r < r_switch) vs the FP64 oracle.
 
 Bars: crossing radius, disk radius and redshift within 1e-4 relative on every stable pixel
 (away from the critical curve and the disk edges: the oracle gives the same outcome at the
-pixel's four corners); image error sum|I - I_ref| / sum|I_ref| <= 1e-3 per frequency;
-ray-status disagreement rate reported and below 1%.
+pixel's four corners); transfer intensities within 1e-4 per stable pixel (pixel_parity.py:
+at least 99.9 % of them, none beyond 1e-3); image error sum|I - I_ref| / sum|I_ref| <= 1e-3
+per frequency; ray-status disagreement rate reported and below 1%.
 """
 import math
 
 import numpy as np
 import pytest
 
+import pixel_parity as P
 from paper_1601_02063_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -81,7 +83,10 @@ def test_thin_disk_mixed_vs_oracle(tracer, orc, r_switch):
     assert np.max(np.abs(got["H_end"])) < 1e-4 and np.max(np.abs(got["Q_drift"])) < 1e-4
 
 
-def test_torus_mixed_image_error(tracer, orc):
+def test_torus_mixed_per_pixel(tracer, orc):
+    """64x64 torus (3 frequencies): every stable pixel's intensity against the oracle at the
+    1e-4 per-pixel bar (at least 99.9 % of them; none beyond 1e-3), image error, statuses and
+    first-crossing radii."""
     sc = W.torus_512(precision="mixed")
     sc.update(n_alpha=64, n_beta=64)
     got, img = _render(tracer, sc)
@@ -92,9 +97,14 @@ def test_torus_mixed_image_error(tracer, orc):
         err = np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum()
         print(f"nu index {k}: image error {err:.3e}")
         assert err <= IMG_ERR
-    assert np.mean(got["status"] != ref["status"]) < STATUS_DISAGREE
-    stable = _stable(orc, sc) & (got["status"] == ref["status"]) & ~np.isnan(ref["r_cross"])
-    assert _rel(got["r_cross"][stable], ref["r_cross"][stable]).max() <= REL_PIXEL
+    disagree = np.mean(got["status"] != ref["status"])
+    print(f"status disagreement {disagree:.4%}")
+    assert disagree < STATUS_DISAGREE
+    stable = P.stable(orc, sc) & (got["status"] == ref["status"])
+    assert stable.mean() > 0.9
+    P.check_planes(img.reshape(3, n), ref["I_nu"][:, :3].T, stable, "torus 64^2")
+    ok = stable & ~np.isnan(ref["r_cross"])
+    assert _rel(got["r_cross"][ok], ref["r_cross"][ok]).max() <= REL_PIXEL
 
 
 def test_mixed_is_schedule_independent(tracer):
@@ -136,13 +146,19 @@ def test_mixed_stats_count_fp64_steps(tracer):
 
 
 def test_mixed_full_size_torus_sampled_pixels(tracer, orc):
-    """The 512x512 torus in the bench's launch: sampled pixels against the oracle."""
+    """The 512x512 torus in the bench's launch: 2,000 sampled pixels against the oracle, each
+    stable one at the 1e-4 per-pixel bar (99.9 %, none beyond 1e-3), and the image error of
+    the sample."""
     sc = W.torus_512(precision="mixed")
     got, img = _render(tracer, sc)
     n = 512 * 512
-    pix = W.sample_pixels(n, 300)
-    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])), pixels=pix)
-    assert np.mean(got["status"][pix] != ref["status"]) < 0.02
+    pix = W.sample_pixels(n, 2000)
+    sc64 = dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"]))
+    ref = orc.render(sc64, pixels=pix)
+    same = got["status"][pix] == ref["status"]
+    assert np.mean(~same) < 0.01
+    stable = P.stable(orc, sc64, pix) & same
+    P.check_planes(img.reshape(3, n)[:, pix], ref["I_nu"][:, :3].T, stable, "torus 512^2 sample")
     for k in range(3):
         I = img[k * n + pix]
         err = np.abs(I - ref["I_nu"][:, k]).sum() / np.abs(ref["I_nu"][:, k]).sum()
@@ -150,33 +166,55 @@ def test_mixed_full_size_torus_sampled_pixels(tracer, orc):
 
 
 def test_mixed_eight_frequency_hard_case(tracer, orc):
-    """Hard case (a = 0.998, i = 85 deg, 8 frequencies) at 64x64 in mixed precision: image error
-    per frequency against the FP64 oracle."""
+    """Hard case (a = 0.998, i = 85 deg, 8 frequencies) at 64x64 in mixed precision: every
+    stable pixel of every frequency plane at the 1e-4 per-pixel bar, and the image error."""
     sc = W.torus_hard_4096(precision="mixed")
     sc.update(n_alpha=64, n_beta=64)
     got, img = _render(tracer, sc)
-    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])))
+    sc64 = dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"]))
+    ref = orc.render(sc64)
     n = 64 * 64
     assert np.mean(got["status"] != ref["status"]) < STATUS_DISAGREE
     for k in range(8):
         I_ref = ref["I_nu"][:, k]
         err = np.abs(img[k * n:(k + 1) * n] - I_ref).sum() / np.abs(I_ref).sum()
         assert err <= IMG_ERR, (k, err)
+    stable = P.stable(orc, sc64) & (got["status"] == ref["status"])
+    P.check_planes(img.reshape(8, n), ref["I_nu"].T, stable, "hard case 64^2")
 
 
 def test_mixed_full_size_hard_case_sampled_pixels(tracer, orc):
-    """The 4096^2 hard case (16.8 M rays, 8 frequencies) in the default launch: 300 sampled
-    pixels against the FP64 oracle, per frequency."""
+    """The 4096^2 hard case (16.8 M rays, 8 frequencies) in the default launch: 2,000 sampled
+    pixels against the FP64 oracle, each stable one at the 1e-4 per-pixel bar per frequency
+    (99.9 %, none beyond 1e-3)."""
     sc = W.torus_hard_4096(precision="mixed")
     got, img = _render(tracer, sc)
     n = 4096 * 4096
-    pix = W.sample_pixels(n, 300, seed=W.SEED + 7)
-    ref = orc.render(dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"])), pixels=pix)
+    pix = W.sample_pixels(n, 2000, seed=W.SEED + 7)
+    sc64 = dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"]))
+    ref = orc.render(sc64, pixels=pix)
     same = got["status"][pix] == ref["status"]
     assert np.mean(same) >= 0.99
-    for k in range(8):
-        rel = _rel(img[k * n + pix][same], ref["I_nu"][same, k])
-        assert np.mean(rel <= 1e-3) >= 0.99 and rel.max() <= 1e-2, (k, rel.max())
+    stable = P.stable(orc, sc64, pix) & same
+    P.check_planes(img.reshape(8, n)[:, pix], ref["I_nu"].T, stable, "hard case 4096^2 sample")
+
+
+def test_photon_ring_pixels_at_the_default_r_switch(tracer, orc):
+    """Pixels whose rays cross the equator more than once (the photon ring's higher-order
+    images: they pass the photon orbit region at a few M) of the hard case at 96x96 over
+    [-8, 8]^2 M, at the default FP32/FP64 split (r_switch = 0: FP32 steps everywhere): each
+    stable ring pixel at the 1e-4 per-pixel bar."""
+    sc = dict(W.torus_hard_4096(precision="mixed"), n_alpha=96, n_beta=96, alpha_min=-8.0,
+              alpha_max=8.0, beta_min=-8.0, beta_max=8.0)
+    assert sc["r_switch"] == 0.0
+    got, img = _render(tracer, sc)
+    sc64 = dict(sc, precision="fp64", C_norm=orc.torus_norm(sc["a"]))
+    ref = orc.render(sc64)
+    n = 96 * 96
+    ring = (ref["n_cross"] >= 2) & (got["status"] == ref["status"])
+    stable = P.stable(orc, sc64) & ring
+    assert stable.sum() > 100
+    P.check_planes(img.reshape(8, n), ref["I_nu"].T, stable, "photon ring 96^2")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

@@ -95,10 +95,12 @@ def test_ragged_shapes(tracer, orc, shape):
     _compare(got, ref)
 
 
-def test_torus_radiative_transfer(tracer, orc):
-    """a=0.94, i=30 deg, analytic torus at nu in {0.5,1,2}, 48x40 over [-20,20]^2."""
+@pytest.mark.parametrize("rt_control", ["controlled", "ride"])
+def test_torus_radiative_transfer(tracer, orc, rt_control):
+    """a=0.94, i=30 deg, analytic torus at nu in {0.5,1,2}, 48x40 over [-20,20]^2, with the
+    intensities under the step control (the default) and riding on the geodesic's steps."""
     sc = W.torus_512()
-    sc.update(n_alpha=48, n_beta=40)
+    sc.update(n_alpha=48, n_beta=40, rt_control=rt_control)
     got, img = _render(tracer, sc)
     sc_o = dict(sc, C_norm=orc.torus_norm(sc["a"]))
     ref = orc.render(sc_o)

@@ -1,12 +1,15 @@
 """Keplerian synchrotron shell (Section 4.5) on the GPU against the oracle, through the C ABI:
-FP64 path pixel by pixel, mixed path by image error and sampled pixels of a full-size image,
-image-integrated spectra.  The oracle evaluates the coefficients in CGS with its own K_2
-(Gauss-Legendre); the CUDA path in scaled units with a trapezoidal K_2."""
+FP64 path pixel by pixel, mixed path pixel by pixel (48x48 and sampled pixels of a full-size
+image, the 1e-4 per-pixel bar on stable pixels), image-integrated spectra.  The oracle
+evaluates the coefficients in CGS with its own K_2 (Gauss-Legendre); the CUDA path works in
+scaled units, its FP64 stages with a trapezoidal sum for K_2 and its FP32 stages with the
+Abramowitz-Stegun polynomial forms of K_0 and K_1."""
 import math
 
 import numpy as np
 import pytest
 
+import pixel_parity as P
 from paper_1601_02063_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +44,13 @@ def _rel(a, b):
 
 @pytest.mark.parametrize("a", [0.0, 0.5, 0.998])
 def test_fp64_shell_matches_oracle(tracer, orc, a):
-    """40 x 36 pixels (ragged tiles) over +-15 M at 150, 340, 1000 GHz."""
+    """40 x 36 pixels (ragged tiles) over +-15 M at 150, 340, 1000 GHz.  The shell's
+    emission jumps where the flow changes from Keplerian to zero-angular-momentum at r_ISCO
+    and at the shell's edge; with the intensities under the step control, each jump is
+    resolved by a cascade of rejected steps whose length depends on where the error
+    estimate falls against 1.  The oracle itself, run at rtol 1e-8 (1 + 1e-14), moves 0.3 %
+    of these pixels by 1e-8 - 2.5e-7 (measured): a reimplementation's rounding does the same,
+    so the bar is 1e-8 on 99 % of the pixels and 1e-6 on all."""
     sc = W.synch_shell(a=a, precision="fp64")
     sc.update(n_alpha=40, n_beta=36)
     got, img = _render(tracer, sc)
@@ -52,7 +61,8 @@ def test_fp64_shell_matches_oracle(tracer, orc, a):
     for k in range(3):
         I_ref, I_got = ref["I_nu"][:, k], img[k * n:(k + 1) * n]
         rel = _rel(I_got[same], I_ref[same])
-        assert np.mean(rel <= REL_INTENSITY) >= STATUS_AGREE and rel.max() <= 1e-6, (k, rel.max())
+        print(f"a={a} plane {k}: {np.mean(rel > REL_INTENSITY):.3%} above 1e-8, max {rel.max():.2e}")
+        assert np.mean(rel <= REL_INTENSITY) >= 0.99 and rel.max() <= 1e-6, (k, rel.max())
         assert I_ref.max() > 0 and np.all(I_got >= 0)
 
 
@@ -69,10 +79,13 @@ def test_spin_batch_equals_single_renders(tracer):
 
 
 @pytest.mark.parametrize("a", [0.0, 0.998])
-def test_mixed_shell_image_error(tracer, orc, a):
+def test_mixed_shell_per_pixel(tracer, orc, a):
+    """48x48 shell images in mixed precision: every stable pixel at the 1e-4 per-pixel bar
+    (99.9 %, none beyond 1e-3) at the three frequencies, and the image error."""
     sc = W.synch_shell(a=a, n=48, precision="mixed")
     got, img = _render(tracer, sc)
-    ref = orc.render(dict(sc, precision="fp64"))
+    sc64 = dict(sc, precision="fp64")
+    ref = orc.render(sc64)
     n = 48 * 48
     for k in range(3):
         I_ref = ref["I_nu"][:, k]
@@ -80,25 +93,23 @@ def test_mixed_shell_image_error(tracer, orc, a):
         print(f"a={a} nu index {k}: image error {err:.3e}")
         assert err <= IMG_ERR
     assert np.mean(got["status"] != ref["status"]) < 0.01
+    stable = P.stable(orc, sc64) & (got["status"] == ref["status"])
+    P.check_planes(img.reshape(3, n), ref["I_nu"][:, :3].T, stable, f"shell a={a} 48^2")
 
 
 def test_mixed_full_size_shell_sampled_pixels(tracer, orc):
-    """The 256 x 256 shell image in the default launch; 300 sampled pixels from the oracle.
-    The transfer terms are not under step control and the FP32 stages step at rtol 1e-6
-    against the oracle's 1e-8, so rays through the hot inner shell differ by the integration
-    error of the steeply varying emissivity.  The oracle itself in FP64 at any tolerance
-    from 1e-6 to 1e-7 puts 3-4 % of these pixels between 1e-3 and 8e-3 from its rtol 1e-8
-    image (the step sequence, not the arithmetic, sets that spread); the image error stays
-    below 1e-3 (test above)."""
+    """The 256 x 256 shell image in the default launch: 1,000 sampled pixels against the
+    oracle, each stable one at the 1e-4 per-pixel bar (99.9 %, none beyond 1e-3)."""
     sc = W.synch_shell(a=0.5, n=256, precision="mixed")
     got, img = _render(tracer, sc)
     n = 256 * 256
-    pix = W.sample_pixels(n, 300)
-    ref = orc.render(dict(sc, precision="fp64"), pixels=pix)
+    pix = W.sample_pixels(n, 1000)
+    sc64 = dict(sc, precision="fp64")
+    ref = orc.render(sc64, pixels=pix)
     same = got["status"][pix] == ref["status"]
-    for k in range(3):
-        rel = _rel(img[k * n + pix][same], ref["I_nu"][same, k])
-        assert np.mean(rel <= 1e-3) >= 0.90 and rel.max() <= 1e-2, (k, rel.max())
+    assert np.mean(same) >= 0.99
+    stable = P.stable(orc, sc64, pix) & same
+    P.check_planes(img.reshape(3, n)[:, pix], ref["I_nu"][:, :3].T, stable, "shell 256^2 sample")
 
 
 def test_shell_spectrum_matches_oracle(tracer, orc):
