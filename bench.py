@@ -383,7 +383,7 @@ def run_ours(args):
     # the plain FP64 path on the same full-size image: its speed, and the production path's
     # accuracy against it (the metric's accuracy condition), per frequency and per pixel
     fp64_info, accuracy = None, None
-    if args.precision != "fp64":
+    if args.precision != "fp64" and args.fp64:
         sc64 = dict(scene, precision="fp64")
         rec64, img64 = tr.alloc(n, B.n_image(scene))
         reps = args.fp64_steps if args.workload == "torus512" else 1
@@ -476,8 +476,10 @@ def run_ours(args):
         from paper_1601_02063_gb300.surrogate import Surrogate
         sg = Surrogate(tr, max_batch=65536)
         t0 = time.perf_counter()
-        xd, td = sg.make_data(1 << 23)
-        loss = sg.train(xd, td, epochs=40, batch=65536, lr=2e-3, lr_final=2e-5)
+        n_train = 1 << 24  # the integrator rays of the training set
+        xd, td = sg.make_data(n_train)
+        loss = sg.train(xd, td, epochs=args.surrogate_epochs, batch=65536, lr=2e-3,
+                        lr_final=2e-5)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         del xd, td
@@ -498,6 +500,29 @@ def run_ours(args):
             holder["r"] = sg.render(sc, out=out_s[:3])
         ms_s = timed(surr, 3)
         img_s, _, _, m_fb = holder["r"]
+        err_s = rel_l1(img_s, ref64)
+        # error against fallback fraction: the critical-curve band widened until every pixel
+        # of the window falls back to the integrator
+        curve = []
+        for band in (0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0):
+            sg.render(sc, band=band, out=out_s[:3])
+            hb = {}
+
+            def surr_b():
+                hb["r"] = sg.render(sc, band=band, out=out_s[:3])
+            ms_b = timed(surr_b, 2)
+            curve.append({"band_M": band, "fallback_fraction": hb["r"][3] / n2,
+                          "image_error_vs_fp64": rel_l1(hb["r"][0], ref64), "ms_per_image": ms_b})
+        # the integrator alone at looser FP32 tolerances: images/s at a given image error
+        loose = []
+        for rt32 in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2):
+            sc_l = dict(sc, rtol_fp32=rt32)
+            tr.render(sc_l, out=(rec2, img2))
+            ms_l = timed(lambda: tr.render(sc_l, out=(rec2, img2)), 2)
+            loose.append({"rtol_fp32": rt32, "ms_per_image": ms_l,
+                          "image_error_vs_fp64": rel_l1(img2[:n2], ref64)})
+        at_equal = [c for c in loose if c["image_error_vs_fp64"] <= err_s]
+        best_int = min(at_equal, key=lambda c: c["ms_per_image"]) if at_equal else None
         # the network alone on the image's 2048^2 input rows (tcgen05 inference kernel)
         mlp_flops = 2.0 * (4 * 256 + 3 * 256 * 256 + 256 * 4) * n2
         xin = torch.rand((n2, 4), dtype=torch.float32, device=f"cuda:{local}")
@@ -509,10 +534,13 @@ def run_ours(args):
         del xin, yout
         surrogate = {
             "workload": "thin disk 2048x2048, a=0.7, i=45 deg, [-20,20]^2",
-            "training": {"rays": 1 << 23, "steps": len(loss), "seconds": t_train,
+            "training": {"rays": n_train, "steps": len(loss), "seconds": t_train,
                          "final_loss": float(loss[-20:].mean())},
             "ms_per_image": ms_s, "images_per_s": 1e3 / ms_s,
-            "fallback_fraction": m_fb / n2, "image_error_vs_fp64": rel_l1(img_s, ref64),
+            "fallback_fraction": m_fb / n2, "image_error_vs_fp64": err_s,
+            "error_vs_fallback": curve,
+            "integrator_at_looser_tolerance": loose,
+            "gain_at_equal_image_error": (best_int["ms_per_image"] / ms_s) if best_int else None,
             "mixed_integrator": {"ms_per_image": ms_mixed, "images_per_s": 1e3 / ms_mixed,
                                  "image_error_vs_fp64": err_mixed},
             "fp64_integrator": {"ms_per_image": ms64, "images_per_s": 1e3 / ms64},
@@ -804,6 +832,8 @@ def main():
     ap.add_argument("--size", type=int, default=0,
                     help="image side override (profiling of smaller cases; 0: the workload's)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU oracle baseline")
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false",
+                    help="omit the FP64 comparison render (profiling runs)")
     ap.add_argument("--split", action="store_true",
                     help="N > 1: split one image into row slabs (strong scaling) instead of "
                          "one image per rank (weak scaling)")
@@ -811,6 +841,8 @@ def main():
                     help="omit the 64-scene batched sweep measurement")
     ap.add_argument("--no-surrogate", dest="surrogate", action="store_false",
                     help="omit training and timing the learned surrogate")
+    ap.add_argument("--surrogate-epochs", type=int, default=40,
+                    help="epochs over the 2^24 training rays")
     ap.add_argument("--no-other", dest="other", action="store_false",
                     help="omit the other torus workload (512^2 torus / 4096^2 hard case)")
     ap.add_argument("--no-spectra", dest="spectra", action="store_false",

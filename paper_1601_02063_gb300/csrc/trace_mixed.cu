@@ -126,7 +126,7 @@ cudaError_t launch_trace_mixed(const TraceArgs &args_in, int32_t nf_slots, const
     }
     args.persistent = L.persistent;
     if (args.chunk <= 0) args.chunk = L.persistent == 3 ? 32 : 8;  // default queue chunk
-    if (L.block > 128) return cudaErrorInvalidValue;
+    if (L.block > kMixedBlock) return cudaErrorInvalidValue;
     if (args.n_total <= 0) return cudaSuccess;
     const unsigned pass_blocks = (unsigned)((args.n_total + 127) / 128);
     mixed_init_kernel<<<pass_blocks, 128, 0, st>>>(args);

@@ -318,6 +318,42 @@ __device__ __forceinline__ void synch32(const Med &m, float r, float nr, float i
 // Hardware reciprocal (relative error ~1 ulp; the FP32 stages run at rtol ~1e-6).
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
 
+// Two independent FP32 operations in one instruction (the packed f32x2 forms of sm_100 and
+// later).  The FMA pipe executes them at the scalar rate, but one issue slot covers both,
+// which is what the FP32 stage loop runs short of (it is issue-bound).  Each lane rounds
+// exactly as fmaf, __fmul_rn and __fadd_rn do.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+        "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 // Low word of s = fl(x + y) (Knuth two-sum).
 __device__ __forceinline__ float two_sum_err(float x, float y, float s)
 {
@@ -470,12 +506,23 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, floa
         // C n_e^2 T_e^-1/2 g^2, and nu0 / T_e per unit observed frequency
         const float Q = m.pref0 * __expf(m.lr_pref * lr + m.c2_pref * c * c) * gg * gg;
         const float xi = ig * m.inv_T0 * __expf(m.T_index * lr);
+        // two frequencies at a time (slot NF of the arrays is padding when NF is odd)
 #pragma unroll
-        for (int k = 0; k < NF; ++k) {
-            const float x = m.nu[k] * xi;
-            const float w = Q * m.inv_nu3[k];  // C n_e^2 T_e^-1/2 / (g nu0^3)
-            ft[k] = 0.5f * w * one_minus_exp(x, __expf(-x));  // Eq. 30
-            fI[k] = w * __expf(-(x + in[4 + k]));             // Eq. 31
+        for (int k = 0; k < NF; k += 2) {
+            const float2 x = mul2(make_float2(m.nu[k], m.nu[k + 1]), dup2(xi));
+            // C n_e^2 T_e^-1/2 / (g nu0^3)
+            const float2 w = mul2(make_float2(m.inv_nu3[k], m.inv_nu3[k + 1]), dup2(Q));
+            const float2 xt = add2(x, make_float2(in[4 + k], k + 1 < NF ? in[5 + k] : 0.f));
+            const float2 om = make_float2(one_minus_exp(x.x, __expf(-x.x)),
+                                          one_minus_exp(x.y, __expf(-x.y)));
+            const float2 ftk = mul2(mul2(dup2(0.5f), w), om);                         // Eq. 30
+            const float2 fIk = mul2(w, make_float2(__expf(-xt.x), __expf(-xt.y)));  // Eq. 31
+            ft[k] = ftk.x;
+            fI[k] = fIk.x;
+            if (k + 1 < NF) {
+                ft[k + 1] = ftk.y;
+                fI[k + 1] = fIk.y;
+            }
         }
     }
 }
@@ -552,73 +599,80 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     }
     const float h = R.hf;
     const float hg = R.sgnf * h;  // geodesic components: dy/ds = sgn f
-    float y0[NG];
-    y0[0] = R.yh[0];
-    y0[1] = R.yh[1];
-    y0[2] = R.yh[4];
-    y0[3] = R.yh[5];
+    // stage inputs in pairs: (r, theta), (p_r, p_theta), (tau_0, tau_1), ... (the last pair's
+    // second slot is padding when NF is odd); the stage sums below use packed FMAs
+    constexpr int NP = (NG + 1) / 2;
+    float2 y0[NP];
+    y0[0] = make_float2(R.yh[0], R.yh[1]);
+    y0[1] = make_float2(R.yh[4], R.yh[5]);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) y0[4 + k] = R.th[k];
-    float in[NG];
+    for (int q = 2; q < NP; ++q) y0[q] = make_float2(R.th[2 * q - 4], R.th[2 * q - 3]);
+    float in[NG + 1];
 #pragma unroll
-    for (int c = 0; c < NG; ++c) in[c] = y0[c];
-    PairStage ps{y0[0], 0.f, y0[1], 0.f, y0[2], 0.f};
-    float acc[5][NG], dy[6], e[6], dtau[NF + 1], dI[NF + 1], eI[NF + 1];
+    for (int q = 0; q < NP; ++q) {
+        in[2 * q] = y0[q].x;
+        in[2 * q + 1] = y0[q].y;
+    }
+    PairStage ps{y0[0].x, 0.f, y0[0].y, 0.f, y0[1].x, 0.f};
+    // acc[J]: weighted slope sums for the input of stage J + 1; de[i] = (dy_i, e_i): fifth-
+    // order sum and error estimate of geodesic component i; dIe[k] = (dI_k, eI_k) of the
+    // intensities; dt[q]: fifth-order sums of tau_2q, tau_2q+1
+    float2 acc[5][NP], de[6], dIe[NF + 1], dt[NP];
 
 #define ODX_ACC(J, COEF)                                                   \
-    _Pragma("unroll") for (int c = 0; c < NG; ++c) acc[J][c] = fmaf((float)(COEF), kf[c], acc[J][c]);
+    _Pragma("unroll") for (int q = 0; q < NP; ++q) acc[J][q] = fma2(dup2((float)(COEF)), kf[q], acc[J][q]);
 #define ODX_NEXT(J)                                                        \
-    _Pragma("unroll") for (int c = 0; c < NG; ++c) in[c] = fmaf(c < 4 ? hg : h, acc[J][c], y0[c]); \
-    ps.tr = __fmul_rn(hg, acc[J][0]);                                      \
-    ps.tt = __fmul_rn(hg, acc[J][1]);                                      \
-    ps.tp = __fmul_rn(hg, acc[J][2]);                                      \
-    in[0] = __fadd_rn(y0[0], ps.tr);                                       \
-    in[1] = __fadd_rn(y0[1], ps.tt);                                       \
-    in[2] = __fadd_rn(y0[2], ps.tp);
-#define ODX_SUMS(B, E)                                                     \
-    _Pragma("unroll") for (int i = 0; i < 6; ++i) {                        \
-        dy[i] = fmaf((float)(B), f[i], dy[i]);                             \
-        e[i] = fmaf((float)(E), f[i], e[i]);                               \
-    }                                                                      \
-    _Pragma("unroll") for (int k = 0; k < NF; ++k) {                       \
-        dtau[k] = fmaf((float)(B), ft[k], dtau[k]);                        \
-        dI[k] = fmaf((float)(B), fI[k], dI[k]);                            \
-        eI[k] = fmaf((float)(E), fI[k], eI[k]);                            \
+    {                                                                      \
+        const float2 tg = mul2(dup2(hg), acc[J][0]);                       \
+        ps.tr = tg.x;                                                      \
+        ps.tt = tg.y;                                                      \
+        ps.tp = __fmul_rn(hg, acc[J][1].x);                                \
+        const float2 rt = add2(y0[0], tg);                                 \
+        in[0] = rt.x;                                                      \
+        in[1] = rt.y;                                                      \
+        in[2] = __fadd_rn(y0[1].x, ps.tp);                                 \
+        in[3] = fmaf(hg, acc[J][1].y, y0[1].y);                            \
+        _Pragma("unroll") for (int q = 2; q < NP; ++q) {                   \
+            const float2 v = fma2(dup2(h), acc[J][q], y0[q]);              \
+            in[2 * q] = v.x;                                               \
+            in[2 * q + 1] = v.y;                                           \
+        }                                                                  \
     }
+#define ODX_SUMS(B, E)                                                     \
+    _Pragma("unroll") for (int i = 0; i < 6; ++i)                          \
+        de[i] = fma2(make_float2((float)(B), (float)(E)), dup2(f[i]), de[i]); \
+    _Pragma("unroll") for (int k = 0; k < NF; ++k)                         \
+        dIe[k] = fma2(make_float2((float)(B), (float)(E)), dup2(fI[k]), dIe[k]); \
+    _Pragma("unroll") for (int q = 2; q < NP; ++q) dt[q] = fma2(dup2((float)(B)), kf[q], dt[q]);
 
 #pragma unroll 1
     for (int st = 0; st < 6; ++st) {
         float f[6], ft[NF + 1], fI[NF + 1];
         derivs32<NF, MK>(g, mf, R.r_isco, in, ps, C, f, ft, fI);
-        float kf[NG];
-        kf[0] = f[0];
-        kf[1] = f[1];
-        kf[2] = f[4];
-        kf[3] = f[5];
+        float2 kf[NP];
+        kf[0] = make_float2(f[0], f[1]);
+        kf[1] = make_float2(f[4], f[5]);
 #pragma unroll
-        for (int k = 0; k < NF; ++k) kf[4 + k] = ft[k];
+        for (int q = 2; q < NP; ++q) kf[q] = make_float2(ft[2 * q - 4], ft[2 * q - 3]);
         switch (st) {
         case 0:
 #pragma unroll
-            for (int c = 0; c < NG; ++c) {
-                acc[0][c] = (float)CK_A21 * kf[c];
-                acc[1][c] = (float)CK_A31 * kf[c];
-                acc[2][c] = (float)CK_A41 * kf[c];
-                acc[3][c] = (float)CK_A51 * kf[c];
-                acc[4][c] = (float)CK_A61 * kf[c];
+            for (int q = 0; q < NP; ++q) {
+                acc[0][q] = mul2(dup2((float)CK_A21), kf[q]);
+                acc[1][q] = mul2(dup2((float)CK_A31), kf[q]);
+                acc[2][q] = mul2(dup2((float)CK_A41), kf[q]);
+                acc[3][q] = mul2(dup2((float)CK_A51), kf[q]);
+                acc[4][q] = mul2(dup2((float)CK_A61), kf[q]);
+                dt[q] = mul2(dup2((float)CK_B1), kf[q]);
             }
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 C.k1[i][t] = R.sgnf * f[i];
-                dy[i] = (float)CK_B1 * f[i];
-                e[i] = (float)CK_E1 * f[i];
+                de[i] = mul2(make_float2((float)CK_B1, (float)CK_E1), dup2(f[i]));
             }
 #pragma unroll
-            for (int k = 0; k < NF; ++k) {
-                dtau[k] = (float)CK_B1 * ft[k];
-                dI[k] = (float)CK_B1 * fI[k];
-                eI[k] = (float)CK_E1 * fI[k];
-            }
+            for (int k = 0; k < NF; ++k)
+                dIe[k] = mul2(make_float2((float)CK_B1, (float)CK_E1), dup2(fI[k]));
             ODX_NEXT(0)
             break;
         case 1:  // b2 = e2 = 0
@@ -644,9 +698,9 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
         case 4:  // b5 = 0
             ODX_ACC(4, CK_A65)
 #pragma unroll
-            for (int i = 0; i < 6; ++i) e[i] = fmaf((float)CK_E5, f[i], e[i]);
+            for (int i = 0; i < 6; ++i) de[i].y = fmaf((float)CK_E5, f[i], de[i].y);
 #pragma unroll
-            for (int k = 0; k < NF; ++k) eI[k] = fmaf((float)CK_E5, fI[k], eI[k]);
+            for (int k = 0; k < NF; ++k) dIe[k].y = fmaf((float)CK_E5, fI[k], dIe[k].y);
             ODX_NEXT(4)
             break;
         default:
@@ -657,6 +711,18 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
 #undef ODX_ACC
 #undef ODX_NEXT
 #undef ODX_SUMS
+    float dy[6], e[6], dtau[NF + 1], dI[NF + 1], eI[NF + 1];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dy[i] = de[i].x;
+        e[i] = de[i].y;
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dI[k] = dIe[k].x;
+        eI[k] = dIe[k].y;
+        dtau[k] = (k & 1) ? dt[2 + k / 2].y : dt[2 + k / 2].x;
+    }
 
     float errmax = 0.f;
     bool nan_err = false;  // fmaxf drops a NaN operand: track it, it rejects the step
