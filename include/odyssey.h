@@ -167,7 +167,7 @@ typedef struct odx_launch {
                               the queue; 3: persistent warps that take 32 consecutive
                               rays once all their lanes are done (warp-coherent
                               queue); 0: one ray per thread, no queue; 2 (auto): 3,
-                              with 4 blocks per SM for mixed launches of 2^19 rays or
+                              with 4 blocks per SM for mixed launches of 2^18 rays or
                               more with up to 3 transfer slots and 3 otherwise      */
     int32_t fp64_batch;    /* ODX_MIXED: a warp runs an FP64 step once this many of
                               its lanes wait for one (or no FP32 lane is left), 1..32 */

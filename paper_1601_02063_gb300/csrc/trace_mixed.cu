@@ -116,13 +116,13 @@ cudaError_t launch_trace_mixed(const TraceArgs &args_in, int32_t nf_slots, const
     TraceArgs args = args_in;
     // launch shape "auto": the warp-coherent queue (a warp takes 32 consecutive rays once all
     // its lanes are done: neighbouring pixels run the same branches together, and the queue
-    // still balances the tail), 4 resident blocks per SM for launches of 2^19 rays or more
-    // with up to 3 transfer slots, 3 otherwise (smaller launches and the 8-slot kernel, which
-    // spills at the 128-register cap)
+    // still balances the tail), 4 resident blocks per SM for launches of 2^18 rays or more
+    // with up to 3 transfer slots, 3 otherwise (smaller launches, and the 8-slot kernel,
+    // whose shared memory admits 3 blocks per SM)
     odx_launch L = L_in;
     if (L.persistent == 2) {
         L.persistent = 3;
-        L.blocks_per_sm = (nf_slots <= 3 && args.n_total >= (1 << 19)) ? 4 : 3;
+        L.blocks_per_sm = (nf_slots <= 3 && args.n_total >= (1 << 18)) ? 4 : 3;
     }
     args.persistent = L.persistent;
     if (args.chunk <= 0) args.chunk = L.persistent == 3 ? 32 : 8;  // default queue chunk

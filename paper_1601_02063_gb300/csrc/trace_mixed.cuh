@@ -107,6 +107,9 @@ struct ColdM {
     float k1[6][kMixedBlock];                 // first stage of the current attempt
     long long id[kMixedBlock];
     int32_t n_cross[kMixedBlock], n64[kMixedBlock];
+    // the Cash-Karp stage-input sums of the current attempt (acc[J]: stage J + 2), in pairs
+    // of components: shared memory keeps them out of the stage loop's registers
+    float2 acc[5][(NF + 5) / 2][kMixedBlock];
 };
 
 template <int NF>
@@ -354,6 +357,16 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b)
 }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
+// 2^a on the special-function unit (PTX ex2.approx.f32, relative error ~2^-22): with the
+// identity e^y = 2^(y log2 e) the scaling of two exponents shares one packed multiply.
+__device__ __forceinline__ float ex2_approx(float a)
+{
+    float d;
+    asm("ex2.approx.f32 %0, %1;" : "=f"(d) : "f"(a));
+    return d;
+}
+constexpr float kLog2e = 1.44269504088896341f;
+
 // Low word of s = fl(x + y) (Knuth two-sum).
 __device__ __forceinline__ float two_sum_err(float x, float y, float s)
 {
@@ -513,10 +526,17 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, floa
             // C n_e^2 T_e^-1/2 / (g nu0^3)
             const float2 w = mul2(make_float2(m.inv_nu3[k], m.inv_nu3[k + 1]), dup2(Q));
             const float2 xt = add2(x, make_float2(in[4 + k], k + 1 < NF ? in[5 + k] : 0.f));
-            const float2 om = make_float2(one_minus_exp(x.x, __expf(-x.x)),
-                                          one_minus_exp(x.y, __expf(-x.y)));
-            const float2 ftk = mul2(mul2(dup2(0.5f), w), om);                         // Eq. 30
-            const float2 fIk = mul2(w, make_float2(__expf(-xt.x), __expf(-xt.y)));  // Eq. 31
+            const float2 ax = mul2(x, dup2(-kLog2e)), at = mul2(xt, dup2(-kLog2e));
+            const float2 em = make_float2(ex2_approx(ax.x), ex2_approx(ax.y));  // e^-x
+            // 1 - e^-x: directly for x > 1/32, else x (1 - x (1/2 - x / 6)) (the subtraction
+            // would lose up to 5 bits there)
+            const float2 big = fma2(em, dup2(-1.f), dup2(1.f));
+            const float2 ser =
+                mul2(x, fma2(x, fma2(x, dup2(1.f / 6.f), dup2(-0.5f)), dup2(1.f)));
+            const float2 om = make_float2(x.x > 0.03125f ? big.x : ser.x,
+                                          x.y > 0.03125f ? big.y : ser.y);
+            const float2 ftk = mul2(mul2(dup2(0.5f), w), om);                        // Eq. 30
+            const float2 fIk = mul2(w, make_float2(ex2_approx(at.x), ex2_approx(at.y)));  // Eq. 31
             ft[k] = ftk.x;
             fI[k] = fIk.x;
             if (k + 1 < NF) {
@@ -617,23 +637,26 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
     // acc[J]: weighted slope sums for the input of stage J + 1; de[i] = (dy_i, e_i): fifth-
     // order sum and error estimate of geodesic component i; dIe[k] = (dI_k, eI_k) of the
     // intensities; dt[q]: fifth-order sums of tau_2q, tau_2q+1
-    float2 acc[5][NP], de[6], dIe[NF + 1], dt[NP];
+    static_assert((NF + 5) / 2 == NP, "pairs of stage inputs");
+    float2 de[6], dIe[NF + 1], dt[NP];
+    auto acc = C.acc;  // [J][pair][thread]
 
 #define ODX_ACC(J, COEF)                                                   \
-    _Pragma("unroll") for (int q = 0; q < NP; ++q) acc[J][q] = fma2(dup2((float)(COEF)), kf[q], acc[J][q]);
+    _Pragma("unroll") for (int q = 0; q < NP; ++q) acc[J][q][t] = fma2(dup2((float)(COEF)), kf[q], acc[J][q][t]);
 #define ODX_NEXT(J)                                                        \
     {                                                                      \
-        const float2 tg = mul2(dup2(hg), acc[J][0]);                       \
+        const float2 a0 = acc[J][0][t], a1 = acc[J][1][t];                 \
+        const float2 tg = mul2(dup2(hg), a0);                              \
         ps.tr = tg.x;                                                      \
         ps.tt = tg.y;                                                      \
-        ps.tp = __fmul_rn(hg, acc[J][1].x);                                \
+        ps.tp = __fmul_rn(hg, a1.x);                                       \
         const float2 rt = add2(y0[0], tg);                                 \
         in[0] = rt.x;                                                      \
         in[1] = rt.y;                                                      \
         in[2] = __fadd_rn(y0[1].x, ps.tp);                                 \
-        in[3] = fmaf(hg, acc[J][1].y, y0[1].y);                            \
+        in[3] = fmaf(hg, a1.y, y0[1].y);                                   \
         _Pragma("unroll") for (int q = 2; q < NP; ++q) {                   \
-            const float2 v = fma2(dup2(h), acc[J][q], y0[q]);              \
+            const float2 v = fma2(dup2(h), acc[J][q][t], y0[q]);           \
             in[2 * q] = v.x;                                               \
             in[2 * q + 1] = v.y;                                           \
         }                                                                  \
@@ -658,11 +681,11 @@ __device__ __forceinline__ int32_t step32(const DevScene &S, RayM<NF> &R, ColdM<
         case 0:
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                acc[0][q] = mul2(dup2((float)CK_A21), kf[q]);
-                acc[1][q] = mul2(dup2((float)CK_A31), kf[q]);
-                acc[2][q] = mul2(dup2((float)CK_A41), kf[q]);
-                acc[3][q] = mul2(dup2((float)CK_A51), kf[q]);
-                acc[4][q] = mul2(dup2((float)CK_A61), kf[q]);
+                acc[0][q][t] = mul2(dup2((float)CK_A21), kf[q]);
+                acc[1][q][t] = mul2(dup2((float)CK_A31), kf[q]);
+                acc[2][q][t] = mul2(dup2((float)CK_A41), kf[q]);
+                acc[3][q][t] = mul2(dup2((float)CK_A51), kf[q]);
+                acc[4][q][t] = mul2(dup2((float)CK_A61), kf[q]);
                 dt[q] = mul2(dup2((float)CK_B1), kf[q]);
             }
 #pragma unroll
