@@ -67,15 +67,19 @@ def measured_peak(key):
         return None
 
 
+TRACER_SOURCES = ("trace_mixed.cuh", "trace_mixed.cu", "trace_mixed_nf0.cu", "trace_mixed_nf3.cu",
+                  "trace_mixed_nf4.cu", "trace_mixed_nf8.cu", "trace_step.cuh", "trace_common.cuh",
+                  "kerr_device.cuh", "odx_internal.h")
+
+
 def kernel_source_hash() -> str:
-    """sha256 (16 hex digits) of the CUDA sources the tracing kernels are built from: a DRAM
-    traffic figure measured by ncu is valid only for the binary built from these."""
-    import glob
+    """sha256 (16 hex digits) of the CUDA sources the mixed tracing kernel is built from: a
+    DRAM traffic figure measured by ncu is valid only for the binary built from these."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_02063_gb300", "csrc")
-    for path in sorted(glob.glob(os.path.join(csrc, "*.cu*")) + glob.glob(os.path.join(csrc, "*.h"))
-                       + [os.path.join(ROOT, "include", "odyssey.h")]):
+    for path in [os.path.join(csrc, f) for f in TRACER_SOURCES] + \
+            [os.path.join(ROOT, "include", "odyssey.h")]:
         h.update(os.path.basename(path).encode())
         with open(path, "rb") as f:
             h.update(f.read())
