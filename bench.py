@@ -78,8 +78,7 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_02063_gb300", "csrc")
-    for path in [os.path.join(csrc, f) for f in TRACER_SOURCES] + \
-            [os.path.join(ROOT, "include", "odyssey.h")]:
+    for path in [os.path.join(csrc, f) for f in TRACER_SOURCES]:
         h.update(os.path.basename(path).encode())
         with open(path, "rb") as f:
             h.update(f.read())

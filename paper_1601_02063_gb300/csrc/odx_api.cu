@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <string>
 #include <thread>
@@ -30,6 +31,7 @@ struct odx_ctx {
     std::vector<DevScene> host_scenes;
     // buffers of odx_render_host
     cudaStream_t host_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // device-to-host copies overlapping the next slab
     void *hbuf = nullptr;
     size_t hbuf_bytes = 0;
     std::string last_error;
@@ -184,7 +186,8 @@ void timing_events(odx_ctx *ctx, cudaStream_t st, cudaEvent_t *e0, cudaEvent_t *
 // Validate, build the scene table, copy it and launch.  Shared by the render and list paths.
 int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const double *rays,
                int64_t n_list, odx_ray_record *records, double *image, cudaStream_t st,
-               int64_t *total_rays, int64_t *total_image)
+               int64_t *total_rays, int64_t *total_image, int64_t id_begin = 0,
+               int64_t id_end = 0)
 {
     const bool list_mode = rays != nullptr || n_list >= 0;
     if (!scenes || n_scenes < 1) return fail(ctx, ODX_ERR_INVALID_ARG, "no scenes");
@@ -229,6 +232,8 @@ int32_t submit(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes, const do
     a.list_mode = list_mode ? 1 : 0;
     a.rays = rays;
     a.n_total = ray;
+    a.id_begin = id_begin;  // a slab of the render (both 0: every ray)
+    a.id_end = id_end;
     a.records = records;
     a.image = image;
     a.queue = ctx->queue;
@@ -484,7 +489,8 @@ int32_t odx_create(odx_ctx **out, int32_t device)
     if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->queue, 256) != cudaSuccess ||
         cudaMalloc(&ctx->stats, sizeof(DevStats)) != cudaSuccess ||
         cudaMemset(ctx->stats, 0, sizeof(DevStats)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
         odx_destroy(ctx);
         return ODX_ERR_CUDA;
     }
@@ -502,6 +508,7 @@ int32_t odx_destroy(odx_ctx *ctx)
     if (ctx->hbuf) cudaFree(ctx->hbuf);
     if (ctx->flux_buf) cudaFree(ctx->flux_buf);
     if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (auto &pr : ctx->events) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
@@ -576,15 +583,53 @@ int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
     }
     odx_ray_record *rec = (odx_ray_record *)ctx->hbuf;
     double *img = (double *)((char *)ctx->hbuf + rec_bytes);
-    rc = submit(ctx, scenes, n_scenes, nullptr, -1, rec, image_host ? img : nullptr,
-                ctx->host_stream, nullptr, nullptr);
-    if (rc != ODX_OK) return rc;
-    ODX_CUDA(ctx, cudaMemcpyAsync(records_host, rec, rec_bytes, cudaMemcpyDeviceToHost,
-                                  ctx->host_stream));
-    if (image_host)
-        ODX_CUDA(ctx, cudaMemcpyAsync(image_host, img, img_bytes, cudaMemcpyDeviceToHost,
+    // A large single image is rendered in slabs of consecutive rays (each slab a launch of
+    // its own over the same scene table, so every ray is computed exactly as in one launch),
+    // and each slab's records and image rows go back to the host on a second stream while
+    // the next slab renders.
+    constexpr int64_t kSlabRays = int64_t(1) << 21;
+    const int64_t slabs = (n_scenes == 1 && nr >= 2 * kSlabRays)
+                              ? std::min<int64_t>(16, (nr + kSlabRays - 1) / kSlabRays)
+                              : 1;
+    if (slabs == 1) {
+        rc = submit(ctx, scenes, n_scenes, nullptr, -1, rec, image_host ? img : nullptr,
+                    ctx->host_stream, nullptr, nullptr);
+        if (rc != ODX_OK) return rc;
+        ODX_CUDA(ctx, cudaMemcpyAsync(records_host, rec, rec_bytes, cudaMemcpyDeviceToHost,
                                       ctx->host_stream));
-    ODX_CUDA(ctx, cudaStreamSynchronize(ctx->host_stream));
+        if (image_host)
+            ODX_CUDA(ctx, cudaMemcpyAsync(image_host, img, img_bytes, cudaMemcpyDeviceToHost,
+                                          ctx->host_stream));
+        ODX_CUDA(ctx, cudaStreamSynchronize(ctx->host_stream));
+        return ODX_OK;
+    }
+    const int64_t planes = odx::scene_planes(scenes[0]);
+    std::vector<cudaEvent_t> done((size_t)slabs, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 0; k < slabs && e == cudaSuccess && rc == ODX_OK; ++k) {
+        const int64_t b = nr * k / slabs, end = nr * (k + 1) / slabs;
+        rc = submit(ctx, scenes, 1, nullptr, -1, rec, image_host ? img : nullptr,
+                    ctx->host_stream, nullptr, nullptr, b, end);
+        if (rc != ODX_OK) break;
+        e = cudaEventCreateWithFlags(&done[(size_t)k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(done[(size_t)k], ctx->host_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, done[(size_t)k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(records_host + b, rec + b, (size_t)(end - b) * sizeof(odx_ray_record),
+                                cudaMemcpyDeviceToHost, ctx->copy_stream);
+        if (e == cudaSuccess && image_host)  // rows b .. end - 1 of every plane
+            e = cudaMemcpy2DAsync(image_host + b, (size_t)nr * sizeof(double), img + b,
+                                  (size_t)nr * sizeof(double), (size_t)(end - b) * sizeof(double),
+                                  (size_t)planes, cudaMemcpyDeviceToHost, ctx->copy_stream);
+    }
+    const cudaError_t e1 = cudaStreamSynchronize(ctx->host_stream);
+    const cudaError_t e2 = cudaStreamSynchronize(ctx->copy_stream);
+    for (cudaEvent_t ev : done)
+        if (ev) cudaEventDestroy(ev);
+    if (rc != ODX_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "slab copy");
+    if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "render stream");
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "copy stream");
     return ODX_OK;
 }
 

@@ -84,7 +84,8 @@ struct TraceArgs {
     int32_t n_scenes;
     int32_t list_mode;     // 1: rays[n][4] = (alpha, beta, a, cos i) with scene 0 as prototype
     const double *rays;
-    int64_t n_total;
+    int64_t n_total;       // rays of the render (all scenes)
+    int64_t id_begin, id_end;  // the global ray ids this launch traces; both 0: [0, n_total)
     odx_ray_record *records;
     double *image;         // may be null
     unsigned long long *queue;
@@ -95,6 +96,16 @@ struct TraceArgs {
     int32_t single_medium;  // 1: every ray uses `med` (one scene, or list mode)
     MedConst med;
 };
+
+// The range of global ray ids a launch traces (id_begin = id_end = 0: every ray).
+__host__ __device__ inline int64_t launch_first(const TraceArgs &a)
+{
+    return a.id_end > 0 ? a.id_begin : 0;
+}
+__host__ __device__ inline int64_t launch_count(const TraceArgs &a)
+{
+    return a.id_end > 0 ? a.id_end - a.id_begin : a.n_total;
+}
 
 // Fill a.single_medium and a.med from the host copy of scene 0.
 void set_launch_medium(TraceArgs &a, const DevScene &scene0, bool single);

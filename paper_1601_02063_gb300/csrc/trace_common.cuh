@@ -32,9 +32,11 @@ struct WarpQueue {
         // warp-coherent queue: a warp takes new rays only once all its lanes are done, so its
         // 32 lanes always trace neighbouring pixels that started together
         if (A.persistent == 3 && __ballot_sync(kFull, live) != 0u) return;
+        // the launch traces global ids first .. first + count - 1; the queue counts from 0
+        const long long first = launch_first(A), count = launch_count(A);
         if (!A.persistent) {
             const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-            if (!live && t < A.n_total) id = t;
+            if (!live && t < count) id = first + t;
             exhausted = true;
             return;
         }
@@ -45,17 +47,17 @@ struct WarpQueue {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(A.queue, (unsigned long long)A.chunk);
                 base = __shfl_sync(kFull, base, 0);
-                if ((long long)base >= A.n_total) {
+                if ((long long)base >= count) {
                     exhausted = true;
                     break;
                 }
                 next = (long long)base;
-                end = min((long long)base + A.chunk, (long long)A.n_total);
+                end = min((long long)base + A.chunk, count);
             }
             const int take = (int)min((long long)__popc(need), end - next);
             const unsigned below = (lane == 0) ? 0u : (0xffffffffu >> (32 - lane));
             const int rank = __popc(need & below);
-            if (((need >> lane) & 1u) && rank < take) id = next + rank;
+            if (((need >> lane) & 1u) && rank < take) id = first + next + rank;
             next += take;
             need &= ~__ballot_sync(kFull, id >= 0);
         }
@@ -238,7 +240,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs &A, int lane, unsign
 inline dim3 trace_grid(const TraceArgs &A, const odx_launch &L, int32_t num_sms)
 {
     if (L.persistent) return dim3((unsigned)(num_sms * L.blocks_per_sm));
-    const long long nb = (A.n_total + L.block - 1) / L.block;
+    const long long nb = (launch_count(A) + L.block - 1) / L.block;
     return dim3((unsigned)(nb > 0 ? nb : 1));
 }
 

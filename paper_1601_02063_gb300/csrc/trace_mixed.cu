@@ -22,8 +22,9 @@ namespace odx {
 // ---- pass 1: FP64 initial state, one ray per thread -------------------------------------
 __global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
 {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= A.n_total) return;
+    const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= launch_count(A)) return;
+    const int64_t id = launch_first(A) + local;
     const DevScene &S = A.scenes[find_scene(A, id)];
     const ObsIn ob = ray_observer(A, S, id);
     const double a = ob.a;
@@ -49,8 +50,9 @@ __global__ void __launch_bounds__(128) mixed_init_kernel(TraceArgs A)
 // ---- pass 3: FP64 checks, redshift, intensity, final records -----------------------------
 __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
 {
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= A.n_total) return;
+    const int64_t local = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (local >= launch_count(A)) return;
+    const int64_t id = launch_first(A) + local;
     const DevScene &S = A.scenes[find_scene(A, id)];
     const MixedOut o = load80<MixedOut>(A.records + id);
     const double a = A.list_mode ? A.rays[4 * id + 2] : S.s.a;
@@ -127,8 +129,8 @@ cudaError_t launch_trace_mixed(const TraceArgs &args_in, int32_t nf_slots, const
     args.persistent = L.persistent;
     if (args.chunk <= 0) args.chunk = L.persistent == 3 ? 32 : 8;  // default queue chunk
     if (L.block > kMixedBlock) return cudaErrorInvalidValue;
-    if (args.n_total <= 0) return cudaSuccess;
-    const unsigned pass_blocks = (unsigned)((args.n_total + 127) / 128);
+    if (launch_count(args) <= 0) return cudaSuccess;
+    const unsigned pass_blocks = (unsigned)((launch_count(args) + 127) / 128);
     mixed_init_kernel<<<pass_blocks, 128, 0, st>>>(args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -207,6 +207,26 @@ def test_render_host_matches_device(tracer):
     assert np.array_equal(himg, img)
 
 
+@pytest.mark.parametrize("n_side", [2048, 2100])
+def test_render_host_slabs_match_device(tracer, n_side):
+    """Images of 2^22 rays or more go to the host in slabs: each slab is a launch of its own
+    over the same scene table while the previous slab's records and image rows are copied
+    back on a second stream.  Every ray is computed as in one launch: the records and the
+    three image planes equal odx_render's bit for bit (mixed-precision torus; 2100^2 gives
+    slab boundaries that are not multiples of a warp)."""
+    import torch
+    from paper_1601_02063_gb300 import binding as B
+    sc = dict(W.torus_512("mixed"), n_alpha=n_side, n_beta=n_side)
+    n = n_side * n_side
+    dev, img = _render(tracer, sc)
+    rec = torch.empty(n * B.RECORD_BYTES // 8, dtype=torch.float64).pin_memory().numpy()
+    rec = rec.view(np.uint8).view(B.RECORD_DTYPE)
+    himg = torch.full((3 * n,), float("nan"), dtype=torch.float64).pin_memory().numpy()
+    B.odx_render_host(tracer.ctx, [sc], rec, himg)
+    assert np.array_equal(rec.view(np.uint8), dev.view(np.uint8))
+    assert np.array_equal(himg, img)
+
+
 @pytest.mark.parametrize("bad", [dict(a=1.0), dict(a=float("nan")), dict(r_obs=5.0),
                                  dict(theta_obs=4.0), dict(n_alpha=0),
                                  dict(alpha_min=3.0, alpha_max=3.0), dict(rtol=0.0),
