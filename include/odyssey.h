@@ -403,11 +403,12 @@ int32_t odx_surrogate_render(odx_mlp *mlp, const odx_scene *scene_host, double b
  * launched).  The caller still provides the outputs (records_dev, image_dev, same layout
  * as odx_render) and the scene descriptions in host memory.  The call works on the calling
  * thread's current device.  Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  The call allocates no device memory and frees none, and copies the scene table
- * into the array with a stream-ordered copy from a buffer on its own stack; while `stream`
- * is capturing a graph it returns ODX_ERR_UNSUPPORTED and does nothing (a replay would
- * copy from that stack frame after the call has returned).
+ * (cudaGetSymbolAddress) and sets the FP64 tracer's shared-memory limit, with that device
+ * current; make that first call before any stream capture.  The call allocates no device
+ * memory and frees none, and copies the scene table into the array with a stream-ordered
+ * copy from a buffer on its own stack; while `stream` is capturing a graph it returns
+ * ODX_ERR_UNSUPPORTED and does nothing (a replay would copy from that stack frame after the
+ * call has returned).
  *
  * Every call shares the one array, which keeps the previous call's contents (the counter is
  * cleared on each call): calls whose work overlaps on the GPU (on different streams, or

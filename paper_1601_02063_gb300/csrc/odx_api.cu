@@ -490,7 +490,8 @@ int32_t odx_create(odx_ctx **out, int32_t device)
         cudaMalloc(&ctx->stats, sizeof(DevStats)) != cudaSuccess ||
         cudaMemset(ctx->stats, 0, sizeof(DevStats)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->host_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        odx::prepare_fp64_kernels() != cudaSuccess) {
         odx_destroy(ctx);
         return ODX_ERR_CUDA;
     }

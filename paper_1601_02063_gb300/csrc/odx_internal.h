@@ -131,6 +131,10 @@ cudaError_t launch_image_flux(const DevScene *scenes_dev, const void *planes_dev
 size_t plane_ref_bytes();
 void fill_plane_ref(void *dst, int64_t first, int64_t n, int32_t scene, int32_t j);
 
+// Set the FP64 tracers' dynamic shared-memory limit on the current device (once per device,
+// before any launch or stream capture).
+cudaError_t prepare_fp64_kernels();
+
 // FMA-chain peak microbenchmark: returns flop/s via *flops (synchronous).
 cudaError_t run_fma_peak(int32_t precision, int32_t num_sms, double *flops);
 

@@ -60,7 +60,8 @@ int32_t device_setup(int dev, DeviceSetup *out)
             return ODX_ERR_CUDA;
         if (major != 10 || minor != 3) return ODX_ERR_NO_DEVICE;
         void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr)
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || ptr == nullptr ||
+            odx::prepare_fp64_kernels() != cudaSuccess)
             return ODX_ERR_CUDA;
         s.scratch = static_cast<unsigned char *>(ptr);
         s.num_sms = sms;

@@ -31,7 +31,7 @@ template <int NF>
 struct Ray64 {
     double y[6];      // r, theta, phi, t, p_r, p_theta
     double k1[6];     // dy/ds at y (first Cash-Karp stage)
-    double tau[NF + 1], I[NF + 1], kt1[NF + 1], kI1[NF + 1];
+    double tau[NF + 1];  // the intensities and the first stage's transfer slopes: shared memory
     double h, hs;     // next step; step used for the error scale of the current step
     double a, L, Q0, sgn;
     double r_start, r_stop, r_in, r_out;
@@ -84,7 +84,7 @@ __device__ __noinline__ void locate_crossing64(const Geo<double> &g, const doubl
 // For the hot spot, inten carries the Gaussian weight w of the entry point.
 template <int NF>
 __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScene &S,
-                                               const Ray64<NF> &R, int32_t status,
+                                               const Ray64<NF> &R, const double *I, int32_t status,
                                                const double yend[6], double r_hit,
                                                double phi_hit, double g, double inten)
 {
@@ -116,7 +116,7 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
             for (int k = 0; k < NF; ++k) {
                 if (k < S.s.n_freq) {
                     const double nu = S.s.freqs[k];
-                    img[(int64_t)k * S.n_rays] = nu * nu * nu * Ij * R.I[k];
+                    img[(int64_t)k * S.n_rays] = nu * nu * nu * Ij * I[k * blockDim.x];
                 }
             }
         } else {
@@ -125,12 +125,154 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     }
 }
 
+// One Cash-Karp attempt as a loop over stages 2-6 around one inlined right-hand side (one
+// copy of the FP64 stage code in the instruction cache).  Each stage's slopes are folded at
+// once into the inputs of the later stages (acc[J]: stage J + 2, in shared memory, layout
+// [J][component][thread], components r, theta, p_r, p_theta, tau_k: t and phi are read by no
+// right-hand side), into the fifth-order sums and into the error estimates, so no stage
+// slope is kept.  Same outputs as ck_attempt.
+template <int NF>
+__device__ __forceinline__ void ck_attempt_fold(const Geo<double> &g, const MediumT<double> &m,
+                                                const double y[6], const double k1[6],
+                                                const double *tau, const double *kt1,
+                                                const double *kI1, int kstride, double h,
+                                                double dy[6], double e[6], double *dtau,
+                                                double *dI, double *eI, double *acc)
+{
+    constexpr int NG = 4 + NF;
+    const int nt = blockDim.x, t = threadIdx.x;
+    auto A_ = [&](int J, int c) -> double & { return acc[(J * NG + c) * nt + t]; };
+    auto kc = [&](const double f[6], const double *ft, int c) {
+        return c < 2 ? f[c] : (c < 4 ? f[c + 2] : ft[c - 4]);
+    };
+    // stage 1 (its transfer slopes kt1, kI1 with stride kstride)
+#pragma unroll
+    for (int c = 0; c < NG; ++c) {
+        const double k = c < 4 ? kc(k1, nullptr, c) : kt1[(c - 4) * kstride];
+        A_(0, c) = CK_A21 * k;
+        A_(1, c) = CK_A31 * k;
+        A_(2, c) = CK_A41 * k;
+        A_(3, c) = CK_A51 * k;
+        A_(4, c) = CK_A61 * k;
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dy[i] = CK_B1 * k1[i];
+        e[i] = CK_E1 * k1[i];
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dtau[k] = CK_B1 * kt1[k * kstride];
+        dI[k] = CK_B1 * kI1[k * kstride];
+        eI[k] = CK_E1 * kI1[k * kstride];
+    }
+#pragma unroll 1
+    for (int st = 1; st < 6; ++st) {  // stages 2..6
+        double yt[6], tt[NF + 1], f[6], ft[NF + 1], fI[NF + 1];
+        yt[0] = y[0] + h * A_(st - 1, 0);
+        yt[1] = y[1] + h * A_(st - 1, 1);
+        yt[2] = y[2];
+        yt[3] = y[3];
+        yt[4] = y[4] + h * A_(st - 1, 2);
+        yt[5] = y[5] + h * A_(st - 1, 3);
+#pragma unroll
+        for (int k = 0; k < NF; ++k) tt[k] = tau[k] + h * A_(st - 1, 4 + k);
+        derivs<double, NF>(g, m, yt, tt, f, ft, fI);
+        double b, ee;  // fifth-order weight and error weight of this stage
+        switch (st) {
+        case 1:  // b2 = e2 = 0
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                const double k = kc(f, ft, c);
+                A_(1, c) += CK_A32 * k;
+                A_(2, c) += CK_A42 * k;
+                A_(3, c) += CK_A52 * k;
+                A_(4, c) += CK_A62 * k;
+            }
+            b = 0.0;
+            ee = 0.0;
+            break;
+        case 2:
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                const double k = kc(f, ft, c);
+                A_(2, c) += CK_A43 * k;
+                A_(3, c) += CK_A53 * k;
+                A_(4, c) += CK_A63 * k;
+            }
+            b = CK_B3;
+            ee = CK_E3;
+            break;
+        case 3:
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                const double k = kc(f, ft, c);
+                A_(3, c) += CK_A54 * k;
+                A_(4, c) += CK_A64 * k;
+            }
+            b = CK_B4;
+            ee = CK_E4;
+            break;
+        case 4:  // b5 = 0
+#pragma unroll
+            for (int c = 0; c < NG; ++c) A_(4, c) += CK_A65 * kc(f, ft, c);
+            b = 0.0;
+            ee = CK_E5;
+            break;
+        default:
+            b = CK_B6;
+            ee = CK_E6;
+            break;
+        }
+        if (st != 1) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                dy[i] += b * f[i];
+                e[i] += ee * f[i];
+            }
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+                dtau[k] += b * ft[k];
+                dI[k] += b * fI[k];
+                eI[k] += ee * fI[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dy[i] *= h;
+        e[i] *= h;
+    }
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        dtau[k] *= h;
+        dI[k] *= h;
+        eI[k] *= h;
+    }
+}
+
+// Shared memory of the FP64 tracer, per thread: the stage-input sums of ck_attempt_fold and
+// the ray's medium constants (read by the right-hand side, kept out of the registers).
+constexpr int kFp64MaxBlock = 256;  // the kernel's launch bound
+inline size_t fp64_smem_bytes(int nf_slots, int block)
+{
+    // without transfer slots the medium is not read: the stage sums alone
+    return ((size_t)(5 * (4 + nf_slots) + 3 * nf_slots) * sizeof(double) +
+            (nf_slots > 0 ? sizeof(MediumT<double>) : 0)) * block;
+}
+
 template <int NF>
 __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
 {
+    extern __shared__ double acc_smem[];
     const int lane = threadIdx.x & 31;
     Ray64<NF> R;
-    MediumT<double> m{};
+    MediumT<double> *meds = reinterpret_cast<MediumT<double> *>(acc_smem + 5 * (4 + NF) * blockDim.x);
+    MediumT<double> &m = meds[threadIdx.x];
+    // per slot k: kt1 at [k], kI1 at [NF + k], the intensity I at [2 NF + k] (stride blockDim.x)
+    double *const rt = reinterpret_cast<double *>(meds + blockDim.x) + threadIdx.x;
+    double *const Kt = rt, *const KI = rt + NF * blockDim.x, *const Is = rt + 2 * NF * blockDim.x;
+    const int ks = blockDim.x;
     bool live = false;
     WarpQueue q;
     q.init(A);
@@ -165,10 +307,20 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             R.phi_cross = qnan();
             R.n_acc = R.n_rej = R.n_cross = 0;
 #pragma unroll
-            for (int k = 0; k < NF + 1; ++k) R.tau[k] = R.I[k] = 0.0;
+            for (int k = 0; k < NF + 1; ++k) R.tau[k] = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) Is[k * ks] = 0.0;
             if constexpr (NF > 0) load_medium_t<double>(S, r_isco, R.r_stop, m);
             const Geo<double> g{R.a, R.L, R.sgn};
-            derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+            {
+                double kt1[NF + 1], kI1[NF + 1];
+                derivs<double, NF>(g, m, R.y, R.tau, R.k1, kt1, kI1);
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    Kt[k * ks] = kt1[k];
+                    KI[k * ks] = kI1[k];
+                }
+            }
             R.h = fmin(S.s.h0, S.s.hmax_frac * R.y[0]);
             if (S.s.emitter == ODX_EMIT_SPOT) R.h = fmin(R.h, spot_step_cap(S.s, R.sgn, R.y));
             R.hs = R.h;
@@ -187,7 +339,8 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             const Geo<double> g{R.a, R.L, R.sgn};
             double y5[6], dy[6], e[6], dtau[NF + 1], dI[NF + 1], eI[NF + 1];
             const double h = R.h;
-            ck_attempt<double, NF>(g, m, R.y, R.k1, R.tau, R.kt1, R.kI1, h, dy, e, dtau, dI, eI);
+            ck_attempt_fold<NF>(g, m, R.y, R.k1, R.tau, Kt, KI, ks, h, dy, e, dtau, dI, eI,
+                                acc_smem);
 #pragma unroll
             for (int i = 0; i < 6; ++i) y5[i] = R.y[i] + dy[i];
             double errmax = 0.0;
@@ -202,7 +355,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
             // the intensities under the step control (ODX_RT_RIDE: infinite floors)
 #pragma unroll
             for (int k = 0; k < NF; ++k) {
-                const double sc = fabs(R.I[k]) + fabs(R.hs * R.kI1[k]) + m.I_floor[k];
+                const double sc = fabs(Is[k * ks]) + fabs(R.hs * KI[k * ks]) + m.I_floor[k];
                 const double v = fabs(eI[k] / sc);
                 nan_err |= isnan(v);
                 errmax = fmax(errmax, v);
@@ -226,7 +379,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                         const double gz = disk_redshift(R.a, yc[0], R.L);
                         const double g2 = gz * gz;
                         const double inten = g2 * g2 * pow(yc[0], -S.s.q_emis);
-                        write_result64<NF>(A, S, R, ODX_DISK_HIT, yc, yc[0], yc[2], gz, inten);
+                        write_result64<NF>(A, S, R, Is, ODX_DISK_HIT, yc, yc[0], yc[2], gz, inten);
                         status = ODX_DISK_HIT;
                     }
                 }
@@ -253,7 +406,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                     spot_region(S.s, R.sgn, yc, d_spot);
                     const double w = S.s.C_norm * exp(-d_spot * d_spot /
                                                       (2.0 * S.s.spot_size * S.s.spot_size));
-                    write_result64<NF>(A, S, R, ODX_DISK_HIT, yc, yc[0], yc[2],
+                    write_result64<NF>(A, S, R, Is, ODX_DISK_HIT, yc, yc[0], yc[2],
                                        spot_redshift(S.s, yc[0], yc[1], R.L), w);
                     status = ODX_DISK_HIT;
                 }
@@ -263,12 +416,18 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
 #pragma unroll
                     for (int k = 0; k < NF; ++k) {
                         R.tau[k] += dtau[k];
-                        R.I[k] += dI[k];
+                        Is[k * ks] += dI[k];
                     }
                     if (R.y[0] < R.r_stop) {
                         status = ODX_CAPTURED;
                     } else {
-                        derivs<double, NF>(g, m, R.y, R.tau, R.k1, R.kt1, R.kI1);
+                        double kt1[NF + 1], kI1[NF + 1];
+                        derivs<double, NF>(g, m, R.y, R.tau, R.k1, kt1, kI1);
+#pragma unroll
+                        for (int k = 0; k < NF; ++k) {
+                            Kt[k * ks] = kt1[k];
+                            KI[k * ks] = kI1[k];
+                        }
                         if (R.k1[0] > 0.0 && R.y[0] > R.r_start) status = ODX_ESCAPED;
                     }
                     R.h = fmin(h_next, S.s.hmax_frac * R.y[0]);
@@ -285,7 +444,7 @@ __global__ void __launch_bounds__(256) trace_fp64_kernel(TraceArgs A)
                 status = ODX_MAXSTEPS;
             if (status != ODX_RUNNING) {
                 if (status != ODX_DISK_HIT)
-                    write_result64<NF>(A, S, R, status, R.y, qnan(), qnan(), qnan(), 0.0);
+                    write_result64<NF>(A, S, R, Is, status, R.y, qnan(), qnan(), qnan(), 0.0);
                 my_rays += 1;
                 my_acc += R.n_acc;
                 my_rej += R.n_rej;
@@ -309,15 +468,32 @@ cudaError_t launch_trace_fp64(const TraceArgs &args_in, int32_t nf_slots, const 
     const dim3 block(L.block);
     const dim3 grid = trace_grid(args, L, num_sms);
     if (ev0) cudaEventRecord(ev0, st);
+    if (L.block > kFp64MaxBlock) return cudaErrorInvalidValue;
+    const size_t smem = fp64_smem_bytes(nf_slots, L.block);
     switch (nf_slots) {
-    case 0: trace_fp64_kernel<0><<<grid, block, 0, st>>>(args); break;
-    case 3: trace_fp64_kernel<3><<<grid, block, 0, st>>>(args); break;
-    case 4: trace_fp64_kernel<4><<<grid, block, 0, st>>>(args); break;
-    case 8: trace_fp64_kernel<8><<<grid, block, 0, st>>>(args); break;
+    case 0: trace_fp64_kernel<0><<<grid, block, smem, st>>>(args); break;
+    case 3: trace_fp64_kernel<3><<<grid, block, smem, st>>>(args); break;
+    case 4: trace_fp64_kernel<4><<<grid, block, smem, st>>>(args); break;
+    case 8: trace_fp64_kernel<8><<<grid, block, smem, st>>>(args); break;
     default: return cudaErrorInvalidValue;
     }
     if (ev1) cudaEventRecord(ev1, st);
     return cudaGetLastError();
+}
+
+// The FP64 tracers take up to 180 KB of dynamic shared memory (more than the default 48 KB)
+// at the largest block: opt in once per device, before any launch or capture.
+cudaError_t prepare_fp64_kernels()
+{
+    const void *fns[4] = {(const void *)trace_fp64_kernel<0>, (const void *)trace_fp64_kernel<3>,
+                          (const void *)trace_fp64_kernel<4>, (const void *)trace_fp64_kernel<8>};
+    const int nf[4] = {0, 3, 4, 8};
+    for (int i = 0; i < 4; ++i) {
+        const cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)fp64_smem_bytes(nf[i], kFp64MaxBlock));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace odx
