@@ -240,10 +240,11 @@ int32_t odx_trace_rays(odx_ctx *ctx, const odx_scene *proto_host, const double *
 /*
  * odx_render with HOST output buffers: copies the scene table in, renders into context
  * buffers and copies records and image back to records_host / image_host (image_host may be
- * NULL).  Synchronous.  Pinned host memory makes the copies faster.  A single scene of 2^22
- * rays or more is rendered in slabs of consecutive rays (up to 16, one launch each over the
- * same scene table, so every ray is computed as in one launch), and each slab's records and
- * image rows are copied back on a second stream while the next slab renders.
+ * NULL).  Synchronous.  Pinned host memory makes the copies faster.  A single scene of 2^23
+ * rays or more is rendered in two slabs of consecutive rays (one launch each over the same
+ * scene table, so every ray is computed as in one launch): the last 7/8 of the rays first,
+ * whose records and image rows are copied back on a second stream while the first 1/8
+ * renders.
  */
 int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes_host, int32_t n_scenes,
                         odx_ray_record *records_host, double *image_host);

@@ -584,14 +584,14 @@ int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
     }
     odx_ray_record *rec = (odx_ray_record *)ctx->hbuf;
     double *img = (double *)((char *)ctx->hbuf + rec_bytes);
-    // A large single image is rendered in slabs of consecutive rays (each slab a launch of
-    // its own over the same scene table, so every ray is computed exactly as in one launch),
-    // and each slab's records and image rows go back to the host on a second stream while
-    // the next slab renders.
-    constexpr int64_t kSlabRays = int64_t(1) << 21;
-    const int64_t slabs = (n_scenes == 1 && nr >= 2 * kSlabRays)
-                              ? std::min<int64_t>(16, (nr + kSlabRays - 1) / kSlabRays)
-                              : 1;
+    // A large single image is rendered in two slabs of consecutive rays, each a launch of its
+    // own over the same scene table (every ray is computed exactly as in one launch): first
+    // the last 7/8 of the rays, then the first 1/8, whose launch hides the device-to-host
+    // copy of the larger slab (~190 GB/s pinned).  Both launches end on rows at the image's
+    // edge, whose rays are short, so neither ends with a long tail of slow rays from the
+    // image's centre; what stays exposed is the copy of the small slab.
+    constexpr int64_t kSlabRays = int64_t(1) << 23;
+    const int64_t slabs = (n_scenes == 1 && nr >= kSlabRays) ? 2 : 1;
     if (slabs == 1) {
         rc = submit(ctx, scenes, n_scenes, nullptr, -1, rec, image_host ? img : nullptr,
                     ctx->host_stream, nullptr, nullptr);
@@ -605,23 +605,25 @@ int32_t odx_render_host(odx_ctx *ctx, const odx_scene *scenes, int32_t n_scenes,
         return ODX_OK;
     }
     const int64_t planes = odx::scene_planes(scenes[0]);
-    std::vector<cudaEvent_t> done((size_t)slabs, nullptr);
+    const int64_t split = nr / 8;
+    const int64_t range[2][2] = {{split, nr}, {0, split}};
+    cudaEvent_t done[2] = {nullptr, nullptr};
     cudaError_t e = cudaSuccess;
-    for (int64_t k = 0; k < slabs && e == cudaSuccess && rc == ODX_OK; ++k) {
-        const int64_t b = nr * k / slabs, end = nr * (k + 1) / slabs;
+    for (int k = 0; k < 2 && e == cudaSuccess && rc == ODX_OK; ++k) {
+        const int64_t b = range[k][0], end = range[k][1];
         rc = submit(ctx, scenes, 1, nullptr, -1, rec, image_host ? img : nullptr,
                     ctx->host_stream, nullptr, nullptr, b, end);
         if (rc != ODX_OK) break;
-        e = cudaEventCreateWithFlags(&done[(size_t)k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(done[(size_t)k], ctx->host_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, done[(size_t)k], 0);
+        e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(done[k], ctx->host_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, done[k], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(records_host + b, rec + b, (size_t)(end - b) * sizeof(odx_ray_record),
                                 cudaMemcpyDeviceToHost, ctx->copy_stream);
-        if (e == cudaSuccess && image_host)  // rows b .. end - 1 of every plane
-            e = cudaMemcpy2DAsync(image_host + b, (size_t)nr * sizeof(double), img + b,
-                                  (size_t)nr * sizeof(double), (size_t)(end - b) * sizeof(double),
-                                  (size_t)planes, cudaMemcpyDeviceToHost, ctx->copy_stream);
+        for (int64_t p = 0; p < planes && e == cudaSuccess && image_host; ++p)  // rays b .. end - 1
+            e = cudaMemcpyAsync(image_host + p * nr + b, img + p * nr + b,
+                                (size_t)(end - b) * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->copy_stream);
     }
     const cudaError_t e1 = cudaStreamSynchronize(ctx->host_stream);
     const cudaError_t e2 = cudaStreamSynchronize(ctx->copy_stream);

@@ -207,13 +207,14 @@ def test_render_host_matches_device(tracer):
     assert np.array_equal(himg, img)
 
 
-@pytest.mark.parametrize("n_side", [2048, 2100])
+@pytest.mark.parametrize("n_side", [2900, 2901])
 def test_render_host_slabs_match_device(tracer, n_side):
-    """Images of 2^22 rays or more go to the host in slabs: each slab is a launch of its own
-    over the same scene table while the previous slab's records and image rows are copied
-    back on a second stream.  Every ray is computed as in one launch: the records and the
-    three image planes equal odx_render's bit for bit (mixed-precision torus; 2100^2 gives
-    slab boundaries that are not multiples of a warp)."""
+    """Images of 2^23 rays or more go to the host in two slabs, the last 7/8 of the rays and
+    then the first 1/8, each a launch of its own over the same scene table, while the first
+    slab's records and image rows are copied back on a second stream.  Every ray is computed
+    as in one launch: the records and the three image planes equal odx_render's bit for bit
+    (mixed-precision torus; at both sizes the slab boundary n/8 is off a multiple of the
+    warp size)."""
     import torch
     from paper_1601_02063_gb300 import binding as B
     sc = dict(W.torus_512("mixed"), n_alpha=n_side, n_beta=n_side)
