@@ -69,7 +69,7 @@ def measured_peak(key):
 
 TRACER_SOURCES = ("trace_mixed.cuh", "trace_mixed.cu", "trace_mixed_nf0.cu", "trace_mixed_nf3.cu",
                   "trace_mixed_nf4.cu", "trace_mixed_nf8.cu", "trace_step.cuh", "trace_common.cuh",
-                  "kerr_device.cuh", "odx_internal.h")
+                  "kerr_device.cuh", "odx_internal.h", "f32x2.cuh")
 
 
 def kernel_source_hash() -> str:
@@ -549,7 +549,7 @@ def run_ours(args):
             "fp64_integrator": {"ms_per_image": ms64, "images_per_s": 1e3 / ms64},
             "mlp_flops_per_image": mlp_flops,
             "mlp_inference": {
-                "kernel": "mlp_forward_tc (tcgen05, accumulator in tensor memory)",
+                "kernel": "mlp_infer_ts (tcgen05, activations and accumulators in tensor memory)",
                 "ms_per_image": ms_mlp, "achieved_tflops": mlp_flops / ms_mlp / 1e9,
                 "peak_tflops": peak_bf16, "frac": (mlp_flops / ms_mlp / 1e9 / peak_bf16)
                 if peak_bf16 else None,

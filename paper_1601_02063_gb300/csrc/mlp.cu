@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "f32x2.cuh"
 #include "kerr_device.cuh"
 #include "odx_internal.h"
 #include "tcgen05.cuh"
@@ -311,31 +312,29 @@ __global__ void scatter_fallback(const odx_ray_record *__restrict__ rec,
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// ---- inference on the fifth-generation tensor cores (tcgen05) ------------------------------
-// One CTA per SM walks 128-row tiles.  Per tile: layer 1 (4 -> 256) on CUDA cores into the
-// activation tile A (shared memory, BF16, K-major core-matrix layout); for each 256 x 256
-// layer the weights W_l^T (packed once into the same layout, 128 KB) arrive by bulk copy,
-// one thread issues 16 MMAs of 128 x 256 x 16 with the FP32 accumulator in tensor memory
-// (256 of its 512 columns), the warps read the accumulator back (bias + SiLU, BF16) into A,
-// or, after the last hidden layer, straight into the 256 -> 4 dot products.  The next
-// layer's weights are loaded while the epilogue runs.  Every wait is bounded: on a time-out
-// the kernel flags *err, waits (bounded) for its own copies and MMAs, frees its tensor
-// memory and returns.
+// ---- training passes on the fifth-generation tensor cores (tcgen05) ----------------------
+// One CTA per SM walks 128-row tiles.  Per tile: layer 1 (4 -> 256) on CUDA cores (or dZ_4
+// from HBM) into the activation tile A (shared memory, BF16, K-major core-matrix layout);
+// for each 256 x 256 layer the weights W_l^T (packed once into the same layout, 128 KB)
+// arrive by bulk copy, one thread issues 16 MMAs of 128 x 256 x 16 with the FP32 accumulator
+// in tensor memory (256 of its 512 columns), the warps read the accumulator back (bias +
+// SiLU, BF16; or SiLU' for the backward pass) into A and HBM.  The next layer's weights are
+// loaded while the epilogue runs.  Every wait is bounded: on a time-out the kernel flags
+// *err, waits (bounded) for its own copies and MMAs, frees its tensor memory and returns.
 constexpr int TC_THREADS = 512, TC_ROWS = 128, TC_CG = TC_THREADS / TC_ROWS;  // column groups
 constexpr int TC_COLS = HID / TC_CG;  // columns of one row per thread (64)
 constexpr uint32_t TC_A_BYTES = TC_ROWS * HID * 2, TC_B_BYTES = HID * HID * 2;
 constexpr uint32_t TC_TMEM_COLS = 256;
 constexpr uint32_t TC_WAIT = 1u << 20;
-// small operands staged in shared memory: W1^T as float4 per column, biases b1..b4,
-// W5 as float4 per input column, b5; layer-5 partial sums of column groups 1..3
-constexpr size_t TC_CONST_BYTES = (HID * 4 + 4 * HID + HID * 4 + 4) * sizeof(float);
-constexpr size_t TC_RED_BYTES = (size_t)(TC_CG - 1) * TC_ROWS * NOUT * sizeof(float);
-constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_B_BYTES + TC_CONST_BYTES + TC_RED_BYTES + 64;
+// small operands staged in shared memory: W1^T as float4 per column, biases b1..b4 (and,
+// for inference, W5 as float4 per input column and b5)
+constexpr size_t TC_CONST_BYTES = (HID * 4 + 4 * HID) * sizeof(float);
+constexpr size_t TC_SMEM = 1024 + TC_A_BYTES + TC_B_BYTES + TC_CONST_BYTES + 64;
 static_assert(TC_SMEM <= 232448, "shared memory of one CTA");
 
-// Three passes share one kernel shape (a 128-row tile through the three 256 x 256 layers):
+// The training passes share one kernel shape (a 128-row tile through the three 256 x 256
+// layers); inference has a kernel of its own (mlp_infer_ts).
 enum TcMode : int {
-    TC_INFER = 0,  // inference: layers 1-5, outputs y
     TC_TRAIN = 1,  // training forward: Z_l and H_l (l = 1..4) kept in HBM for the backward pass
     TC_BWD = 2,    // backward: dZ_4 -> dZ_3, dZ_2, dZ_1 through W_4^T, W_3^T, W_2^T and SiLU'
 };
@@ -346,7 +345,7 @@ struct TcArgs {
     const float *p;     // FP32 parameters (biases)
     const bf16 *wpack;  // the three packed B operands in the order of use, 128 KB each
     int64_t n_rows;
-    float *y;           // TC_INFER: outputs [n][4]
+    float *y;           // inference: outputs [n][4]
     bf16 *Z[5], *H[5];  // TC_TRAIN: written (l = 1..4); TC_BWD: Z_1..Z_3 read
     const bf16 *dZ4;    // TC_BWD: input
     bf16 *dZ[5];        // TC_BWD: dZ_3, dZ_2, dZ_1 written
@@ -358,7 +357,7 @@ struct TcArgs {
 // (dh = dz W^T).  Either way the K-major core-matrix layout, one 128 KB block per layer,
 // blocks in the order the pass uses them (forward l = 2, 3, 4; backward l = 4, 3, 2).
 __global__ void pack_hidden_weights(const bf16 *__restrict__ pb, bf16 *__restrict__ wpack,
-                                    int backward)
+                                    int backward, float scale)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 3 * HID * HID) return;
@@ -366,7 +365,8 @@ __global__ void pack_hidden_weights(const bf16 *__restrict__ pb, bf16 *__restric
     const int k = e / HID, n = e % HID;  // W_l[k][n]
     const int l = backward ? 4 - i : 2 + i;
     const uint32_t off = backward ? tc::kmajor_offset(k, n, HID) : tc::kmajor_offset(n, k, HID);
-    wpack[(size_t)i * HID * HID + off / 2] = pb[off_w(l) + k * HID + n];
+    wpack[(size_t)i * HID * HID + off / 2] =
+        __float2bfloat16_rn(__bfloat162float(pb[off_w(l) + k * HID + n]) * scale);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
@@ -420,11 +420,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
     unsigned char *sB = sA + TC_A_BYTES;
     float4 *sW1 = reinterpret_cast<float4 *>(sB + TC_B_BYTES);  // [256]
     float *sBias = reinterpret_cast<float *>(sW1 + HID);         // [4][256]: b1..b4
-    float4 *sW5 = reinterpret_cast<float4 *>(sBias + 4 * HID);  // [256]
-    float *sB5 = reinterpret_cast<float *>(sW5 + HID);          // [4]
-    float *red = sB5 + 4;                                        // [TC_CG-1][128][4]
     uint64_t *bars = reinterpret_cast<uint64_t *>(
-        ((uintptr_t)(red + (TC_CG - 1) * TC_ROWS * NOUT) + 7) & ~(uintptr_t)7);
+        ((uintptr_t)(sBias + 4 * HID) + 7) & ~(uintptr_t)7);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -443,10 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
                                  bfv(A.pb, OFF_W1 + 2 * HID + n), bfv(A.pb, OFF_W1 + 3 * HID + n));
             sBias[n] = A.p[OFF_B1 + n];
             for (int l = 2; l <= 4; ++l) sBias[(l - 1) * HID + n] = A.p[off_b(l) + n];
-            sW5[n] = make_float4(bfv(A.pb, OFF_W5 + n * NOUT + 0), bfv(A.pb, OFF_W5 + n * NOUT + 1),
-                                 bfv(A.pb, OFF_W5 + n * NOUT + 2), bfv(A.pb, OFF_W5 + n * NOUT + 3));
         }
-        if (tid < NOUT) sB5[tid] = A.p[OFF_B5 + tid];
     }
     if (warp == 0) tc::tmem_alloc(tslot, TC_TMEM_COLS);
     tc::fence_before_sync();
@@ -523,7 +517,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
             }
         }
         tc::fence_proxy_async();
-        float acc5[NOUT] = {0.f, 0.f, 0.f, 0.f};
         for (int i = 0; i < 3; ++i) {
             // A tile written and previous accumulator reads done; weights present
             bool to = false;
@@ -640,47 +633,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
                                     pack8(h + 8 * q);
                         }
                     }
-                    if constexpr (MODE == TC_INFER) {
-                        if (i == 2) {  // layer 5 (256 -> 4) on the BF16-rounded activations
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const float hb = __bfloat162float(__float2bfloat16_rn(h[j]));
-                                const float4 w = sW5[nb + j];
-                                acc5[0] += hb * w.x;
-                                acc5[1] += hb * w.y;
-                                acc5[2] += hb * w.z;
-                                acc5[3] += hb * w.w;
-                            }
-                        }
-                    }
                 }
             }
             tc::fence_proxy_async();
             tc::fence_before_sync();
         }
         if (failed) break;
-        if constexpr (MODE == TC_INFER) {
-            // ---- layer 5: combine the column groups of each row -----------------------------
-            if (cg > 0) {
-#pragma unroll
-                for (int o = 0; o < NOUT; ++o) red[((cg - 1) * TC_ROWS + r) * NOUT + o] = acc5[o];
-            }
-            __syncthreads();
-            if (cg == 0) {
-                const int64_t gr = tile * TC_ROWS + r;
-                if (gr < n_rows) {
-                    float out[NOUT];
-#pragma unroll
-                    for (int o = 0; o < NOUT; ++o) {
-                        out[o] = acc5[o] + sB5[o];
-#pragma unroll
-                        for (int g = 0; g < TC_CG - 1; ++g) out[o] += red[(g * TC_ROWS + r) * NOUT + o];
-                    }
-                    *reinterpret_cast<float4 *>(A.y + gr * NOUT) =
-                        make_float4(out[0], out[1], out[2], out[3]);
-                }
-            }
-        }
     }
     // ---- teardown: nothing of ours in flight, then free the tensor memory -------------------
     if (tid == 0) {
@@ -693,6 +651,337 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
+}
+
+// ---- inference with the activations in tensor memory -------------------------------------
+// One CTA per SM walks 128-row tiles.  Tensor memory (512 columns) holds two FP32
+// accumulators of 128 x 128 (the two column halves of a 256-wide layer's output, columns
+// 0-127 and 128-255) and two BF16 activation tiles of 128 x 256 (two values per 32-bit
+// column, 128 columns each), so each 256 x 256 layer takes its A operand from tensor memory
+// (tcgen05.mma with A in TMEM) and shared memory holds only weights: the two 64 KB column
+// halves of one packed W^T.  One control thread issues the weight copies and the MMAs; two
+// groups of 8 epilogue warps, one per accumulator half, each read their half back (bias +
+// SiLU, BF16) into the other activation tile as soon as its MMAs are done, independently of
+// the other half, and compute their half of layer 1 (4 -> 256) of the next tile while the
+// last 256 x 256 layer of this one runs.  Per layer and column
+// half h the control thread issues K = 0..127 once the epilogue has written that half of
+// the input, K = 128..255 once it has written the other, then commits; the weight half is
+// refilled with the next layer's as soon as its MMAs are done.  Hand-offs go through
+// mbarriers (each completes at most one phase ahead of its waiter); every wait is bounded,
+// and on a time-out the CTA flags *err, drains its own MMAs and copies (bounded) and frees
+// its tensor memory.
+constexpr int TS_EPI = 512, TS_THREADS = TS_EPI + 32;  // 16 epilogue warps + the control warp
+constexpr uint32_t TS_WH_BYTES = TC_B_BYTES / 2;        // a column half of a packed W^T: 64 KB
+constexpr uint32_t TS_ABUF = 256;                        // activation tiles at columns 256, 384
+constexpr size_t TS_RED_BYTES = 2 * (size_t)(TC_CG - 1) * TC_ROWS * NOUT * sizeof(float);
+constexpr size_t TS_CONST_BYTES = TC_CONST_BYTES + (HID * 4 + 4) * sizeof(float);
+constexpr size_t TS_SMEM = 1024 + 2 * TS_WH_BYTES + TS_CONST_BYTES + TS_RED_BYTES + 128;
+static_assert(TS_SMEM <= 232448, "shared memory of one CTA");
+// mbarriers: wfull[h] weight half present, accfull[h] accumulator half complete, afree[h]
+// accumulator half read out, aready[h] / l1ready[h] K-half h of the next layer's input
+// written by a hidden-layer epilogue / by layer 1, redfull the layer-5 partial sums of
+// column quarters 1..3 written, drain (teardown)
+enum : int { TS_WFULL = 0, TS_ACCFULL = 2, TS_AFREE = 4, TS_AREADY = 6, TS_L1READY = 8,
+             TS_REDFULL = 10, TS_DRAIN = 11, TS_NBAR = 12 };
+constexpr int TS_GROUP_WARPS = TS_EPI / 64;  // epilogue warps per accumulator half
+// waits sleep up to TS_SLEEP_NS per try when the poll limit is at least TS_SLEEP_POLLS (a
+// limit below that, a test's, polls without sleeping)
+constexpr uint32_t TS_SLEEP_NS = 1000, TS_SLEEP_POLLS = 4096;
+
+// Activation tile holding the input of layer i (0..2: layers 2..4) of a tile whose parity
+// among this CTA's tiles is par; layer 1 writes the input of i = 0.
+__device__ __forceinline__ uint32_t ts_in_col(uint32_t par, int i)
+{
+    return TS_ABUF + 128u * ((par + (i == 1 ? 1u : 0u)) & 1u);
+}
+
+__global__ void __launch_bounds__(TS_THREADS, 1) mlp_infer_ts(const __grid_constant__ TcArgs A)
+{
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    unsigned char *sW = reinterpret_cast<unsigned char *>(
+        ((uintptr_t)ts_raw + 1023) & ~(uintptr_t)1023);          // [2][64 KB]
+    float4 *sW1 = reinterpret_cast<float4 *>(sW + 2 * TS_WH_BYTES);  // [128][2]: column pairs
+    float *sBias = reinterpret_cast<float *>(sW1 + HID);             // [4][256]: b1..b4
+    float4 *sW5 = reinterpret_cast<float4 *>(sBias + 4 * HID);      // [256]
+    float *sB5 = reinterpret_cast<float *>(sW5 + HID);              // [4]
+    float *red = sB5 + 4;                                            // [2][TC_CG-1][128][4]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        ((uintptr_t)(red + 2 * (TC_CG - 1) * TC_ROWS * NOUT) + 7) & ~(uintptr_t)7);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + TS_NBAR);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n_rows = A.n_rows;
+    const int64_t n_tiles = (n_rows + TC_ROWS - 1) / TC_ROWS;
+    auto bar = [&](int k) { return tc::smem_u32(&bars[k]); };
+    if (tid == 0) {
+        for (int h = 0; h < 2; ++h) {
+            tc::mbar_init(bar(TS_WFULL + h), 1);
+            tc::mbar_init(bar(TS_ACCFULL + h), 1);
+            tc::mbar_init(bar(TS_AFREE + h), TS_GROUP_WARPS);
+            tc::mbar_init(bar(TS_AREADY + h), TS_GROUP_WARPS);
+            tc::mbar_init(bar(TS_L1READY + h), TS_GROUP_WARPS);
+        }
+        tc::mbar_init(bar(TS_REDFULL), 3 * TS_GROUP_WARPS / 2);  // the warps of quarters 1..3
+        tc::mbar_init(bar(TS_DRAIN), 1);
+        tc::mbar_fence_init();
+    }
+    // layers 1-4 halved (exactly), as the packed W^T: every pre-activation comes out as z / 2
+    // W1 by column pairs (n, n + 1): {W1[0][n], W1[0][n+1], W1[1][n], W1[1][n+1]},
+    // {W1[2][n], W1[2][n+1], W1[3][n], W1[3][n+1]}
+    for (int q = tid; q < HID; q += TS_THREADS) {
+        const int n = 2 * (q >> 1), k0 = 2 * (q & 1);
+        auto w = [&](int k, int c) { return 0.5f * bfv(A.pb, OFF_W1 + k * HID + c); };
+        sW1[q] = make_float4(w(k0, n), w(k0, n + 1), w(k0 + 1, n), w(k0 + 1, n + 1));
+    }
+    for (int n = tid; n < HID; n += TS_THREADS) {
+        sBias[n] = 0.5f * A.p[OFF_B1 + n];
+        for (int l = 2; l <= 4; ++l) sBias[(l - 1) * HID + n] = 0.5f * A.p[off_b(l) + n];
+        sW5[n] = make_float4(bfv(A.pb, OFF_W5 + n * NOUT + 0), bfv(A.pb, OFF_W5 + n * NOUT + 1),
+                             bfv(A.pb, OFF_W5 + n * NOUT + 2), bfv(A.pb, OFF_W5 + n * NOUT + 3));
+    }
+    if (tid < NOUT) sB5[tid] = A.p[OFF_B5 + tid];
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int64_t first = blockIdx.x, stride = gridDim.x;
+    bool failed = false;
+    const uint32_t sleep_ns = A.wait_limit >= TS_SLEEP_POLLS ? TS_SLEEP_NS : 0u;
+    auto mwait = [&](int k, uint32_t ph) {
+        return sleep_ns ? tc::mbar_wait_sleep(bar(k), ph, A.wait_limit, sleep_ns)
+                        : tc::mbar_wait(bar(k), ph, A.wait_limit);
+    };
+
+    if (warp == TS_EPI / 32) {
+        // ---- control thread: weight copies and MMAs ---------------------------------------
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, HID / 2);
+            const uint32_t w_base = tc::smem_u32(sW);
+            uint32_t ph_w[2] = {0u, 0u}, ph_acc[2] = {0u, 0u}, ph_af[2] = {0u, 0u},
+                     ph_ar[2] = {0u, 0u}, ph_l1[2] = {0u, 0u};
+            bool w_pend[2] = {false, false}, acc_used = false, ok = true;
+            auto wait = [&](int k, uint32_t &ph) {
+                if (!mwait(k, ph)) return false;
+                ph ^= 1u;
+                return true;
+            };
+            auto load_half = [&](int blk, int h) {  // packed block blk (layer blk + 2), half h
+                tc::mbar_expect_tx(bar(TS_WFULL + h), TS_WH_BYTES);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    tc::bulk_g2s(w_base + h * TS_WH_BYTES + c * (TS_WH_BYTES / 4),
+                                 A.wpack + (size_t)blk * HID * HID + (size_t)h * (HID * HID / 2) +
+                                     (size_t)c * (HID * HID / 8),
+                                 TS_WH_BYTES / 4, bar(TS_WFULL + h));
+                w_pend[h] = true;
+            };
+            // B descriptors of the two weight halves; K step j starts 256 bytes further
+            // (the start-address field counts 16-byte units)
+            const uint64_t bdesc[2] = {
+                tc::smem_desc(w_base, 128, (HID / 8) * 128),
+                tc::smem_desc(w_base + TS_WH_BYTES, 128, (HID / 8) * 128)};
+            auto mmas8 = [&](uint32_t d, uint32_t a, uint64_t bd, int j0) {  // K steps j0..j0+7
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    tc::mma_bf16_ts(d, a + 8 * (j0 + j), bd + (uint64_t)(16 * (j0 + j)), idesc,
+                                    (j0 + j) > 0 ? 1u : 0u);
+            };
+            if (first < n_tiles) {
+                load_half(0, 0);
+                load_half(0, 1);
+            }
+            for (int64_t tile = first; tile < n_tiles && ok; tile += stride) {
+                const uint32_t par = (uint32_t)((tile - first) / stride) & 1u;
+                for (int i = 0; i < 3 && ok; ++i) {
+                    const uint32_t a_col = ts_in_col(par, i);
+                    const int rdy = i == 0 ? TS_L1READY : TS_AREADY;
+                    uint32_t *ph_rdy = i == 0 ? ph_l1 : ph_ar;
+                    // column half 0: K 0..127 once its input half is written, then K 128..255
+                    ok = wait(rdy, ph_rdy[0]) && (!acc_used || wait(TS_AFREE, ph_af[0])) &&
+                         wait(TS_WFULL, ph_w[0]);
+                    if (!ok) break;
+                    w_pend[0] = false;
+                    tc::fence_after_sync();
+                    mmas8(tmem, tmem + a_col, bdesc[0], 0);
+                    ok = wait(rdy + 1, ph_rdy[1]);
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    mmas8(tmem, tmem + a_col, bdesc[0], 8);
+                    tc::mma_commit(bar(TS_ACCFULL + 0));
+                    // column half 1: the whole input is written by now
+                    ok = (!acc_used || wait(TS_AFREE + 1, ph_af[1])) && wait(TS_WFULL + 1, ph_w[1]);
+                    if (!ok) break;
+                    w_pend[1] = false;
+                    tc::fence_after_sync();
+                    mmas8(tmem + 128, tmem + a_col, bdesc[1], 0);
+                    mmas8(tmem + 128, tmem + a_col, bdesc[1], 8);
+                    tc::mma_commit(bar(TS_ACCFULL + 1));
+                    acc_used = true;
+                    // refill each weight half with the next layer's once its MMAs are done
+                    const bool more = i < 2 || tile + stride < n_tiles;
+                    for (int h = 0; h < 2 && ok; ++h) {
+                        ok = wait(TS_ACCFULL + h, ph_acc[h]);
+                        if (ok && more) load_half((i + 1) % 3, h);
+                    }
+                }
+            }
+            failed = !ok;
+            // drain: every MMA issued here complete, every copy landed (bounded)
+            tc::mma_commit(bar(TS_DRAIN));
+            tc::mbar_wait(bar(TS_DRAIN), 0, TC_WAIT);
+            for (int h = 0; h < 2; ++h)
+                if (w_pend[h]) tc::mbar_wait(bar(TS_WFULL + h), ph_w[h], TC_WAIT);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue warps: group g = accumulator half g, row r (TMEM lane), columns
+        //      cq * 64 .. +63 of the half.  Each warp waits for its own hand-offs. -----------
+        const int g = warp >> 3, lg = warp & 3, cq = (warp >> 2) & 1;
+        const int r = 32 * lg + lane;
+        const uint32_t lane_off = (uint32_t)(32 * lg) << 16;
+        uint32_t ph_acc = 0u, ph_red = 0u;
+        auto warp_wait = [&](int k, uint32_t &ph) {  // bounded; lane 0 polls for the warp
+            int ok = 1;
+            if (lane == 0) ok = mwait(k, ph) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            __syncwarp();
+            if (ok) ph ^= 1u;
+            return ok != 0;
+        };
+        auto load_x = [&](int64_t tile) {
+            const int64_t gr = tile * TC_ROWS + r;
+            return (tile < n_tiles && gr < n_rows)
+                       ? *reinterpret_cast<const float4 *>(A.x + gr * NIN)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        auto arrive = [&](int k) {  // this warp's tensor- and shared-memory writes are done
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(bar(k));
+        };
+        // layer 1 (4 -> 256) of a tile, this warp's columns, into the activation tile at a_col
+        auto layer1 = [&](float4 xi, uint32_t a_col) {
+#pragma unroll 1
+            for (int c = 0; c < 2; ++c) {
+                uint32_t packed[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {  // columns n, n + 1
+                    const int n = g * 128 + cq * 64 + c * 32 + 2 * j;
+                    const float4 w01 = sW1[n], w23 = sW1[n + 1];
+                    float2 z = *reinterpret_cast<const float2 *>(sBias + n);
+                    z = fma2(dup2(xi.x), make_float2(w01.x, w01.y), z);
+                    z = fma2(dup2(xi.y), make_float2(w01.z, w01.w), z);
+                    z = fma2(dup2(xi.z), make_float2(w23.x, w23.y), z);
+                    z = fma2(dup2(xi.w), make_float2(w23.z, w23.w), z);
+                    const float2 h = fma2(z, make_float2(tanh_fast(z.x), tanh_fast(z.y)), z);
+                    packed[j] = pack_bf16x2(h.x, h.y);
+                }
+                tc::tmem_st16(tmem + lane_off + a_col + g * 64 + cq * 32 + c * 16, packed);
+            }
+            tc::tmem_st_wait();
+            arrive(TS_L1READY + g);
+        };
+        if (first < n_tiles) layer1(load_x(first), ts_in_col(0, 0));
+        for (int64_t tile = first; tile < n_tiles && !failed; tile += stride) {
+            const uint32_t par = (uint32_t)((tile - first) / stride) & 1u;
+            const float4 x_next = load_x(tile + stride);  // in flight through two layers
+            float2 acc01 = make_float2(0.f, 0.f), acc23 = make_float2(0.f, 0.f);  // layer 5
+            for (int i = 0; i < 3; ++i) {
+                const float *bias = sBias + (i + 1) * HID;  // layer i + 2
+                if (!warp_wait(TS_ACCFULL + g, ph_acc)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t acc = tmem + lane_off + 128u * g + cq * 64;
+                const uint32_t a_out = ts_in_col(par, i + 1) + g * 64 + cq * 32;
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {  // 32 columns at a time
+                    uint32_t v[2][16];
+                    tc::tmem_ld16(acc + 32 * c, v[0]);
+                    tc::tmem_ld16(acc + 32 * c + 16, v[1]);
+                    tc::tmem_ld_wait();
+                    if (c == 1) arrive(TS_AFREE + g);
+                    const int nb = g * 128 + cq * 64 + 32 * c;  // output column of v[0][0]
+                    if (i < 2) {
+                        uint32_t packed[16];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int n = nb + 16 * u + 2 * j;
+                                const float2 hz = add2(make_float2(__uint_as_float(v[u][2 * j]),
+                                                                   __uint_as_float(v[u][2 * j + 1])),
+                                                       *reinterpret_cast<const float2 *>(bias + n));
+                                const float2 h =
+                                    fma2(hz, make_float2(tanh_fast(hz.x), tanh_fast(hz.y)), hz);
+                                packed[8 * u + j] = pack_bf16x2(h.x, h.y);
+                            }
+                        }
+                        tc::tmem_st16(tmem + lane_off + a_out + 16 * c, packed);
+                    } else {  // layer 5 (256 -> 4) on the BF16-rounded activations
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int n = nb + 16 * u + 2 * j;
+                                const float2 hz = add2(make_float2(__uint_as_float(v[u][2 * j]),
+                                                                   __uint_as_float(v[u][2 * j + 1])),
+                                                       *reinterpret_cast<const float2 *>(bias + n));
+                                const float2 h =
+                                    fma2(hz, make_float2(tanh_fast(hz.x), tanh_fast(hz.y)), hz);
+                                const float2 hb = __bfloat1622float2(__floats2bfloat162_rn(h.x, h.y));
+                                const float4 w0 = sW5[n], w1 = sW5[n + 1];
+                                acc01 = fma2(dup2(hb.x), make_float2(w0.x, w0.y), acc01);
+                                acc23 = fma2(dup2(hb.x), make_float2(w0.z, w0.w), acc23);
+                                acc01 = fma2(dup2(hb.y), make_float2(w1.x, w1.y), acc01);
+                                acc23 = fma2(dup2(hb.y), make_float2(w1.z, w1.w), acc23);
+                            }
+                        }
+                    }
+                }
+                if (i < 2) {
+                    tc::tmem_st_wait();
+                    arrive(TS_AREADY + g);
+                }
+                // the next tile's layer 1 runs while this tile's last layer is on the tensor cores
+                if (i == 1 && tile + stride < n_tiles) layer1(x_next, ts_in_col(par ^ 1u, 0));
+            }
+            if (failed) break;
+            // ---- layer 5: the four column quarters of each row, added in quarter order ---------
+            float *rb = red + (size_t)par * (TC_CG - 1) * TC_ROWS * NOUT;
+            const int quarter = 2 * g + cq;
+            if (quarter > 0) {
+                *reinterpret_cast<float4 *>(rb + ((quarter - 1) * TC_ROWS + r) * NOUT) =
+                    make_float4(acc01.x, acc01.y, acc23.x, acc23.y);
+                arrive(TS_REDFULL);
+            } else {
+                if (!warp_wait(TS_REDFULL, ph_red)) {
+                    failed = true;
+                    break;
+                }
+                const int64_t gr = tile * TC_ROWS + r;
+                if (gr < n_rows) {
+                    const float acc5[NOUT] = {acc01.x, acc01.y, acc23.x, acc23.y};
+                    float out[NOUT];
+#pragma unroll
+                    for (int o = 0; o < NOUT; ++o) {
+                        out[o] = acc5[o] + sB5[o];
+#pragma unroll
+                        for (int q = 0; q < TC_CG - 1; ++q) out[o] += rb[(q * TC_ROWS + r) * NOUT + o];
+                    }
+                    *reinterpret_cast<float4 *>(A.y + gr * NOUT) =
+                        make_float4(out[0], out[1], out[2], out[3]);
+                }
+            }
+        }
+    }
+    if (failed) atomicExch(A.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---- layer 5 (256 -> 4), the loss and the column reductions on CUDA cores -----------------
@@ -1068,13 +1357,11 @@ TcArgs chain_args(odx_mlp *m, const bf16 *wpack, int64_t n)
     return a;
 }
 
-// Training forward over B rows (B multiple of 128) on the tensor cores, Z_l and H_l kept;
-// then layer 5 with the loss and dL/dy (targets t).
-// Training forward pass of B rows (targets t[B][8]): Z_l, H_l kept for the backward pass,
-// the loss partials, dL/dy and dL/dZ4.
+// Training forward pass of B rows (B a multiple of 128, targets t[B][8]) on the tensor
+// cores: Z_l, H_l kept for the backward pass, the loss partials, dL/dy and dL/dZ4.
 void forward(odx_mlp *m, const float *x, int64_t B, const float *t, cudaStream_t st)
 {
-    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0);
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0, 1.f);
     TcArgs a = chain_args(m, m->wpack, B);
     a.x = x;
     launch_chain<TC_TRAIN>(m, a, B, st);
@@ -1088,7 +1375,7 @@ void forward(odx_mlp *m, const float *x, int64_t B, const float *t, cudaStream_t
 // the batch, partials added in split order); bias and 4-wide-layer gradients as column sums.
 void backward(odx_mlp *m, const float *x, int64_t B, cudaStream_t st)
 {
-    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpackB, 1);
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpackB, 1, 1.f);
     TcArgs a = chain_args(m, m->wpackB, B);
     a.dZ4 = m->dZ[4];
     launch_chain<TC_BWD>(m, a, B, st);
@@ -1147,15 +1434,18 @@ int32_t take_tc_flag(odx_mlp *m)
     return ODX_ERR_DEVICE_FLAG;
 }
 
-// Inference of n rows on the tensor cores (weights packed from the current BF16 copy).
+// Inference of n rows on the tensor cores (weights packed from the current BF16 copy, halved:
+// the kernel's accumulators then hold z / 2, the argument of SiLU's tanh form).
 void infer_tc(odx_mlp *m, const float *x, int64_t n, float *y, cudaStream_t st)
 {
     if (n <= 0) return;
-    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0);
+    pack_hidden_weights<<<blocks_for(3 * HID * HID, 256), 256, 0, st>>>(m->pb, m->wpack, 0, 0.5f);
     TcArgs a = chain_args(m, m->wpack, n);
     a.x = x;
     a.y = y;
-    launch_chain<TC_INFER>(m, a, n, st);
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, std::max(1, m->num_sms));
+    mlp_infer_ts<<<grid, TS_THREADS, TS_SMEM, st>>>(a);
 }
 
 }  // namespace
@@ -1202,8 +1492,8 @@ int32_t odx_mlp_create(odx_ctx *ctx, int64_t max_batch, uint64_t seed, odx_mlp *
     }
     cudaMemset(m->m1, 0, NPARAM * sizeof(float));
     cudaMemset(m->m2, 0, NPARAM * sizeof(float));
-    if (cudaFuncSetAttribute(mlp_chain_tc<TC_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TC_SMEM) != cudaSuccess ||
+    if (cudaFuncSetAttribute(mlp_infer_ts, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TS_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(mlp_chain_tc<TC_TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TC_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(mlp_chain_tc<TC_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,

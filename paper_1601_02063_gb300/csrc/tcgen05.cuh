@@ -1,6 +1,6 @@
 // Thin wrappers around the sm_100-family tensor-core instructions (tcgen05: TMEM allocation,
 // MMA with the accumulator in tensor memory, loads back to registers), mbarriers and the
-// bulk (non-tensor) asynchronous copy, as inline PTX.  Used by the MLP inference kernel.
+// bulk (non-tensor) asynchronous copy, as inline PTX.  Used by the MLP kernels.
 //
 // Operand layouts used here (no swizzle), both built from 8 x 8 "core matrices" of BF16
 // (128 contiguous bytes); LBO is the byte stride between core matrices along K, SBO along
@@ -95,6 +95,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// The same with the A operand in tensor memory (128 lanes = rows, K along the columns, two
+// BF16 per 32-bit column, the even k in the low half): taddr_a is the column of k = 0.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t tmem_d, uint32_t taddr_a, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "r"(taddr_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // Arrive once on the mbarrier when all previously issued MMAs of this thread are complete.
 __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
@@ -117,6 +128,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t v[16])
 __device__ __forceinline__ void tmem_ld_wait()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns from registers: thread t writes lane (base + t).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t v[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ---- mbarriers and bulk copies ------------------------------------------------------------
@@ -144,6 +170,28 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// Plain (non-transaction) arrival of this thread on the mbarrier, release at CTA scope.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+// The same, each try suspending the thread up to hint_ns nanoseconds until the phase
+// completes (the thread sleeps instead of spinning; it resumes when the phase completes).
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, uint32_t max_tries,
+                                                uint32_t hint_ns)
+{
+    for (uint32_t i = 0; i < max_tries; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity), "r"(hint_ns)
             : "memory");
         if (done) return true;
     }

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "f32x2.cuh"
 #include "kerr_device.cuh"
 #include "odx_internal.h"
 #include "trace_common.cuh"
@@ -321,41 +322,6 @@ __device__ __forceinline__ void synch32(const Med &m, float r, float nr, float i
 // Hardware reciprocal (relative error ~1 ulp; the FP32 stages run at rtol ~1e-6).
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.f, x); }
 
-// Two independent FP32 operations in one instruction (the packed f32x2 forms of sm_100 and
-// later).  The FMA pipe executes them at the scalar rate, but one issue slot covers both,
-// which is what the FP32 stage loop runs short of (it is issue-bound).  Each lane rounds
-// exactly as fmaf, __fmul_rn and __fadd_rn do.
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
-        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
-        "fma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
-        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
-        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 add2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
-        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
-        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
 // 2^a on the special-function unit (PTX ex2.approx.f32, relative error ~2^-22): with the
 // identity e^y = 2^(y log2 e) the scaling of two exponents shares one packed multiply.

@@ -45,8 +45,9 @@ def test_sync_deadline_runs_out_then_completes(tracer):
 
 def test_tensor_core_wait_limit_raises_the_flag(tracer):
     """Inference with the in-loop tensor-core waits limited to one poll: the kernel gives up
-    at its first wait (the weights' bulk copy is still in flight), raises the flag, waits for
-    its own copies and MMAs with the default limit and frees its tensor memory.  The next
+    at its first waits (for the first tile's input, the weights' bulk copy or the first
+    MMAs, none of which is done one poll after it is issued), raises the flag, waits for its
+    own copies and MMAs with the default limit and frees its tensor memory.  The next
     synchronous call reports ODX_ERR_DEVICE_FLAG and clears it; with the limit restored the
     same inference returns the same outputs as before."""
     import torch
