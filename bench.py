@@ -810,7 +810,8 @@ def run_ours(args):
                      "pipe": "fp64" if args.precision == "fp64" else "fp32"},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": SCENE_TABLE_BYTES,
-                "d2h_bytes_per_step": n * B.RECORD_BYTES + 8 * B.n_image(scene)},
+                "d2h_bytes_per_step": n * B.RECORD_BYTES + 8 * B.n_image(scene),
+                "ms_per_call": [round(t * 1e3, 2) for t in e2e_s]},
         "clocks": clk,
         "cpu_baseline": cpu,
         "paper_context": {"value": 16.31, "unit": "ns per RK step (runtime / total steps)",

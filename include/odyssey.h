@@ -346,14 +346,16 @@ int32_t odx_mlp_destroy(odx_mlp *mlp);
 int32_t odx_mlp_get_params(odx_mlp *mlp, float *params_host);
 int32_t odx_mlp_set_params(odx_mlp *mlp, const float *params_host); /* resets Adam state */
 /* y_dev[n][4] = MLP(x_dev[n][4]), any n, on the tensor cores (tcgen05: 128-row tiles, the
- * FP32 accumulator in tensor memory); x_dev and y_dev 16-byte aligned (else INVALID_ARG).
+ * FP32 accumulators and the BF16 activations in tensor memory); x_dev and y_dev 16-byte
+ * aligned (else INVALID_ARG).
  * Asynchronous on `stream`.  A tensor-core wait that times out leaves its tile's outputs
  * unwritten and raises a device flag, reported (and cleared) as ODX_ERR_DEVICE_FLAG by the
  * next odx_mlp_get_params, odx_mlp_gradients or odx_surrogate_render call. */
 int32_t odx_mlp_forward(odx_mlp *mlp, const float *x_dev, int64_t n, float *y_dev, void *stream);
 /* Test hook for the tensor-core kernels' failure path: the number of polls after which a
  * wait inside the tile loop of the forward and backward chains (odx_mlp_forward,
- * odx_mlp_train_step, odx_mlp_gradients) gives up; 0 restores the default, 2^20 polls.  A
+ * odx_mlp_train_step, odx_mlp_gradients) gives up; 0 restores the default, 2^20 polls (the
+ * inference kernel sleeps up to 1 us in each poll of 4,096 or more, and not below).  A
  * kernel that gives up raises the device flag and returns after waiting, with the default
  * limit, for its own copies and MMAs in flight and freeing its tensor memory; the flag is
  * reported as above.  No counterpart in the paper. */
