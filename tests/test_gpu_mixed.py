@@ -109,20 +109,28 @@ def test_torus_mixed_per_pixel(tracer, orc):
 
 def test_mixed_is_schedule_independent(tracer):
     """The FP32/FP64 choice is made per ray from its own radius, so records do not depend on
-    the launch shape or on which rays share a warp: bitwise equal within one kernel binary.
-    Register-cap variants (blocks_per_sm) are different binaries in which the compiler may
-    fuse multiply-adds differently, so across them the bar is the FP32 rounding level."""
+    the launch shape or on which rays share a warp: bitwise equal within one kernel binary,
+    records and image planes (thin disk with FP64 steps, and a 3-frequency torus whose
+    intensities are under the step control).  Register-cap variants
+    (blocks_per_sm) are different binaries in which the compiler may fuse multiply-adds
+    differently, so across them the bar is the FP32 rounding level."""
     from paper_1601_02063_gb300 import binding as B
-    sc = W.scene(n_alpha=40, n_beta=33, precision="mixed", r_switch=3.0)
-    base, _ = _render(tracer, sc)
     saved = B.odx_get_launch(tracer.ctx)
     try:
-        for launch in (dict(fp64_batch=1, chunk=7), dict(persistent=0, block=64),
-                       dict(fp64_batch=32, chunk=128), dict(persistent=1, chunk=8),
-                       dict(persistent=3, chunk=32)):
-            tracer.set_launch(**dict(saved, **launch))
-            got, _ = _render(tracer, sc)
-            assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), launch
+        for sc in (W.scene(n_alpha=40, n_beta=33, precision="mixed", r_switch=3.0),
+                   dict(W.torus_512("mixed"), n_alpha=40, n_beta=33)):
+            tracer.set_launch(**saved)
+            base, base_img = _render(tracer, sc)
+            for launch in (dict(fp64_batch=1, chunk=7), dict(persistent=0, block=64),
+                           dict(fp64_batch=32, chunk=128), dict(persistent=1, chunk=8),
+                           dict(persistent=3, chunk=32)):
+                tracer.set_launch(**dict(saved, **launch))
+                got, img = _render(tracer, sc)
+                assert np.array_equal(got.view(np.uint8), base.view(np.uint8)), (sc["emitter"], launch)
+                assert np.array_equal(img, base_img), (sc["emitter"], launch)
+        sc = W.scene(n_alpha=40, n_beta=33, precision="mixed", r_switch=3.0)
+        tracer.set_launch(**saved)
+        base, _ = _render(tracer, sc)
         for bps in (2, 3):
             tracer.set_launch(**dict(saved, blocks_per_sm=bps))
             got, _ = _render(tracer, sc)
