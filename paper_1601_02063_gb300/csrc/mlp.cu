@@ -659,17 +659,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) mlp_chain_tc(const __grid_const
 // 0-127 and 128-255) and two BF16 activation tiles of 128 x 256 (two values per 32-bit
 // column, 128 columns each), so each 256 x 256 layer takes its A operand from tensor memory
 // (tcgen05.mma with A in TMEM) and shared memory holds only weights: the two 64 KB column
-// halves of one packed W^T.  One control thread issues the weight copies and the MMAs; two
-// groups of 8 epilogue warps, one per accumulator half, each read their half back (bias +
-// SiLU, BF16) into the other activation tile as soon as its MMAs are done, independently of
-// the other half, and compute their half of layer 1 (4 -> 256) of the next tile while the
-// last 256 x 256 layer of this one runs.  Per layer and column
-// half h the control thread issues K = 0..127 once the epilogue has written that half of
-// the input, K = 128..255 once it has written the other, then commits; the weight half is
-// refilled with the next layer's as soon as its MMAs are done.  Hand-offs go through
-// mbarriers (each completes at most one phase ahead of its waiter); every wait is bounded,
-// and on a time-out the CTA flags *err, drains its own MMAs and copies (bounded) and frees
-// its tensor memory.
+// halves of one packed W^T.  One control thread issues the weight copies and the MMAs: per
+// layer and column half, K = 0..127 once the epilogue has written that half of the input,
+// K = 128..255 once it has written the other, then a commit; each weight half is refilled
+// with the next layer's as soon as its MMAs are done.  Two groups of 8 epilogue warps, one
+// per accumulator half, each read their half back into the other activation tile as soon as
+// its MMAs are done, independently of the other half, and compute their half of layer 1
+// (4 -> 256) of the next tile while the last 256 x 256 layer of this one runs.  The weights
+// and biases of layers 1-4 come halved (exact), so the accumulators hold z / 2 and SiLU is
+// z/2 (1 + tanh(z/2)): per pair of activations one packed add (bias), two tanh, one packed
+// FMA and one BF16 pack.  Hand-offs go through mbarriers (each completes at most one phase
+// ahead of its waiter); every wait is bounded, and on a time-out the CTA flags *err, drains
+// its own MMAs and copies (bounded) and frees its tensor memory.
 constexpr int TS_EPI = 512, TS_THREADS = TS_EPI + 32;  // 16 epilogue warps + the control warp
 constexpr uint32_t TS_WH_BYTES = TC_B_BYTES / 2;        // a column half of a packed W^T: 64 KB
 constexpr uint32_t TS_ABUF = 256;                        // activation tiles at columns 256, 384
