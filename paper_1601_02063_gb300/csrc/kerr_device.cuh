@@ -169,19 +169,22 @@ __device__ __forceinline__ InitOut init_ray(const ObsIn &o, double sgn)
     const double th = acos(c);
     const double ph = atan2(yp, xp);
     const double s = fmax(sqrt(fmax((1.0 - c) * (1.0 + c), 0.0)), kSinFloor);
-    const double rho = sqrt(xp * xp + yp * yp);
-    const double cph = rho > 0.0 ? xp / rho : 1.0, sph = rho > 0.0 ? yp / rho : 0.0;
+    const double rho2 = xp * xp + yp * yp;
+    const double irho = rho2 > 0.0 ? rsqrt(rho2) : 0.0;
+    const double cph = rho2 > 0.0 ? xp * irho : 1.0, sph = rho2 > 0.0 ? yp * irho : 0.0;
     const double cP = cph * o.cpo + sph * o.spo;  // cos(phi - phi_obs)
     const double sP = sph * o.cpo - cph * o.spo;  // sin(phi - phi_obs)
     const double R = sqrt(r * r + a * a);
     const double Sig = r * r + a * a * c * c;
     const double Del = r * r - 2.0 * r + a * a;
-    double rd = sgn * (-(r * R * s * sto * cP + R * R * c * cto) / Sig);
-    double td = sgn * ((r * s * cto - R * c * sto * cP) / Sig);
+    // FP64 divisions are long sequences on this part: each reciprocal is taken once
+    const double iSig = 1.0 / Sig, iDel = 1.0 / Del;
+    double rd = sgn * (-(r * R * s * sto * cP + R * R * c * cto) * iSig);
+    double td = sgn * ((r * s * cto - R * c * sto * cP) * iSig);
     double pd = sgn * (sto * sP / (R * s));
-    const double E2 = ((Sig - 2.0 * r) / (Sig * Del)) * (Sig * rd * rd + Sig * Del * td * td) +
+    const double E2 = ((Sig - 2.0 * r) * iSig * iDel) * (Sig * rd * rd + Sig * Del * td * td) +
                       Del * pd * pd * s * s;
-    const double iE = 1.0 / sqrt(E2);
+    const double iE = rsqrt(E2);
     rd *= iE;
     td *= iE;
     pd *= iE;
@@ -191,32 +194,35 @@ __device__ __forceinline__ InitOut init_ray(const ObsIn &o, double sgn)
     out.y[1] = th;
     out.y[2] = ph;
     out.y[3] = 0.0;
-    out.y[4] = Sig * rd / Del;
+    out.y[4] = Sig * rd * iDel;
     out.y[5] = Sig * td;
-    out.Q = out.y[5] * out.y[5] + (out.L * out.L / (s * s) - a * a) * c * c;
+    const double Ls = out.L / s;
+    out.Q = out.y[5] * out.y[5] + (Ls * Ls - a * a) * c * c;
     return out;
 }
 
-// Relative null violation and relative Carter-constant drift at the end of a ray.
-__device__ __forceinline__ double null_violation(double a, double L, const double y[6])
-{
-    const double s = fmax(sin(y[1]), kSinFloor);
-    const double r = y[0];
-    const double Del = r * r - 2.0 * r + a * a;
-    const double t1 = Del * y[4] * y[4], t2 = y[5] * y[5];
-    const double q = L / s - a * s;
-    const double t3 = q * q;
-    const double P = r * r + a * a - a * L;
-    const double t4 = P * P / Del;
-    return (t1 + t2 + t3 - t4) / (fabs(t1) + t2 + t3 + fabs(t4));
-}
-
-__device__ __forceinline__ double carter_q(double a, double L, const double y[6])
+// At the end of a ray (state y): the relative null violation H and the Carter constant Q,
+// from one sincos of theta.
+struct EndChecks {
+    double H, Q;
+};
+__device__ __forceinline__ EndChecks end_checks(double a, double L, const double y[6])
 {
     double s, c;
     sincos(y[1], &s, &c);
     s = fmax(s, kSinFloor);
-    return y[5] * y[5] + (L * L / (s * s) - a * a) * c * c;
+    const double r = y[0];
+    const double Del = r * r - 2.0 * r + a * a;
+    const double t1 = Del * y[4] * y[4], t2 = y[5] * y[5];
+    const double Ls = L / s;
+    const double q = Ls - a * s;
+    const double t3 = q * q;
+    const double P = r * r + a * a - a * L;
+    const double t4 = P * P / Del;
+    EndChecks e;
+    e.H = (t1 + t2 + t3 - t4) / (fabs(t1) + t2 + t3 + fabs(t4));
+    e.Q = t2 + (Ls * Ls - a * a) * c * c;
+    return e;
 }
 
 // ---- thermal synchrotron shell (Section 4.5) ---------------------------------------------

@@ -99,8 +99,9 @@ __device__ __forceinline__ void write_result64(const TraceArgs &A, const DevScen
     o.phi_hit = phi_hit;
     o.g = g;
     o.intensity = inten;
-    o.H_end = null_violation(R.a, R.L, yend);
-    o.Q_drift = (carter_q(R.a, R.L, yend) - R.Q0) / fmax(fabs(R.Q0), 1.0);
+    const EndChecks ec = end_checks(R.a, R.L, yend);
+    o.H_end = ec.H;
+    o.Q_drift = (ec.Q - R.Q0) / fmax(fabs(R.Q0), 1.0);
     double *img = A.image ? A.image + S.img_offset + (R.id - S.ray_begin) : nullptr;
     if (S.s.emitter == ODX_EMIT_NT_DISK)
         o.intensity = nt_disk_planes(S, img, R.a, ray_r_isco(A, S, R.a), r_hit, g,

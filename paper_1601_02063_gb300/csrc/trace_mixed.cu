@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(128) mixed_finish_kernel(TraceArgs A)
     r.n_cross = o.n_cross;
     r.r_cross = (double)o.rc;
     r.phi_cross = (double)o.pc;
-    r.H_end = null_violation(a, L, yend);
-    r.Q_drift = (carter_q(a, L, yend) - Q0) / fmax(fabs(Q0), 1.0);
+    const EndChecks ec = end_checks(a, L, yend);
+    r.H_end = ec.H;
+    r.Q_drift = (ec.Q - Q0) / fmax(fabs(Q0), 1.0);
     r.r_hit = r.phi_hit = r.g = qnan();
     r.intensity = 0.0;
     if (o.status == ODX_DISK_HIT && S.s.emitter == ODX_EMIT_SPOT) {
