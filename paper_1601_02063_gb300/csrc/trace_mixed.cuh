@@ -491,17 +491,18 @@ __device__ __forceinline__ void derivs32(const Geo<float> &g, const Med &m, floa
             const float2 x = mul2(make_float2(m.nu[k], m.nu[k + 1]), dup2(xi));
             // C n_e^2 T_e^-1/2 / (g nu0^3)
             const float2 w = mul2(make_float2(m.inv_nu3[k], m.inv_nu3[k + 1]), dup2(Q));
-            const float2 xt = add2(x, make_float2(in[4 + k], k + 1 < NF ? in[5 + k] : 0.f));
-            const float2 ax = mul2(x, dup2(-kLog2e)), at = mul2(xt, dup2(-kLog2e));
+            const float2 tau = make_float2(in[4 + k], k + 1 < NF ? in[5 + k] : 0.f);
+            // exponents in base 2: -x log2(e) and -(x + tau) log2(e)
+            const float2 ax = mul2(x, dup2(-kLog2e)), at = fma2(tau, dup2(-kLog2e), ax);
             const float2 em = make_float2(ex2_approx(ax.x), ex2_approx(ax.y));  // e^-x
-            // 1 - e^-x: directly for x > 1/32, else x (1 - x (1/2 - x / 6)) (the subtraction
-            // would lose up to 5 bits there)
-            const float2 big = fma2(em, dup2(-1.f), dup2(1.f));
+            // (1 - e^-x) / 2: directly for x > 1/32, else x (1/2 - x (1/4 - x / 12)) (the
+            // subtraction would lose up to 5 bits there); the halving is exact either way
+            const float2 big = fma2(em, dup2(-0.5f), dup2(0.5f));
             const float2 ser =
-                mul2(x, fma2(x, fma2(x, dup2(1.f / 6.f), dup2(-0.5f)), dup2(1.f)));
+                mul2(x, fma2(x, fma2(x, dup2(1.f / 12.f), dup2(-0.25f)), dup2(0.5f)));
             const float2 om = make_float2(x.x > 0.03125f ? big.x : ser.x,
                                           x.y > 0.03125f ? big.y : ser.y);
-            const float2 ftk = mul2(mul2(dup2(0.5f), w), om);                        // Eq. 30
+            const float2 ftk = mul2(w, om);                                          // Eq. 30
             const float2 fIk = mul2(w, make_float2(ex2_approx(at.x), ex2_approx(at.y)));  // Eq. 31
             ft[k] = ftk.x;
             fI[k] = fIk.x;
