@@ -681,9 +681,10 @@ static_assert(TS_SMEM <= 232448, "shared memory of one CTA");
 // mbarriers: wfull[h] weight half present, accfull[h] accumulator half complete, afree[h]
 // accumulator half read out, aready[h] / l1ready[h] K-half h of the next layer's input
 // written by a hidden-layer epilogue / by layer 1, redfull the layer-5 partial sums of
-// column quarters 1..3 written, drain (teardown)
+// column quarters 1..3 written, l1go the tensor cores done with layer 3 (both halves; its
+// input tile takes the next tile's layer 1), drain (teardown)
 enum : int { TS_WFULL = 0, TS_ACCFULL = 2, TS_AFREE = 4, TS_AREADY = 6, TS_L1READY = 8,
-             TS_REDFULL = 10, TS_DRAIN = 11, TS_NBAR = 12 };
+             TS_REDFULL = 10, TS_L1GO = 11, TS_DRAIN = 12, TS_NBAR = 13 };
 constexpr int TS_GROUP_WARPS = TS_EPI / 64;  // epilogue warps per accumulator half
 // waits sleep up to TS_SLEEP_NS per try when the poll limit is at least TS_SLEEP_POLLS (a
 // limit below that, a test's, polls without sleeping)
@@ -723,6 +724,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) mlp_infer_ts(const __grid_const
             tc::mbar_init(bar(TS_L1READY + h), TS_GROUP_WARPS);
         }
         tc::mbar_init(bar(TS_REDFULL), 3 * TS_GROUP_WARPS / 2);  // the warps of quarters 1..3
+        tc::mbar_init(bar(TS_L1GO), 1);
         tc::mbar_init(bar(TS_DRAIN), 1);
         tc::mbar_fence_init();
     }
@@ -818,6 +820,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) mlp_infer_ts(const __grid_const
                     mmas8(tmem + 128, tmem + a_col, bdesc[1], 0);
                     mmas8(tmem + 128, tmem + a_col, bdesc[1], 8);
                     tc::mma_commit(bar(TS_ACCFULL + 1));
+                    if (i == 1 && tile + stride < n_tiles) tc::mma_commit(bar(TS_L1GO));
                     acc_used = true;
                     // refill each weight half with the next layer's once its MMAs are done
                     const bool more = i < 2 || tile + stride < n_tiles;
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1) mlp_infer_ts(const __grid_const
         const int g = warp >> 3, lg = warp & 3, cq = (warp >> 2) & 1;
         const int r = 32 * lg + lane;
         const uint32_t lane_off = (uint32_t)(32 * lg) << 16;
-        uint32_t ph_acc = 0u, ph_red = 0u;
+        uint32_t ph_acc = 0u, ph_red = 0u, ph_go = 0u;
         auto warp_wait = [&](int k, uint32_t &ph) {  // bounded; lane 0 polls for the warp
             int ok = 1;
             if (lane == 0) ok = mwait(k, ph) ? 1 : 0;
@@ -946,8 +949,16 @@ __global__ void __launch_bounds__(TS_THREADS, 1) mlp_infer_ts(const __grid_const
                     tc::tmem_st_wait();
                     arrive(TS_AREADY + g);
                 }
-                // the next tile's layer 1 runs while this tile's last layer is on the tensor cores
-                if (i == 1 && tile + stride < n_tiles) layer1(x_next, ts_in_col(par ^ 1u, 0));
+                // the next tile's layer 1 runs while this tile's last layer is on the tensor
+                // cores, into the tile that layer 3 read: once both its halves are done
+                if (i == 1 && tile + stride < n_tiles) {
+                    if (!warp_wait(TS_L1GO, ph_go)) {
+                        failed = true;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    layer1(x_next, ts_in_col(par ^ 1u, 0));
+                }
             }
             if (failed) break;
             // ---- layer 5: the four column quarters of each row, added in quarter order ---------
